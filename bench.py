@@ -1,0 +1,272 @@
+#!/usr/bin/env python3
+"""Benchmark: phi/c_s/c_l cell-updates per second of the fused explicit step.
+
+Workload (one step = one forward-Euler step of the whole hot path over the
+grid): 3D 256^3 FP32, spherical solid seed of radius 20 cells with seeded
+surface noise, k_e = 0.1, undercooling 0.5 of the freezing range, D_s/D_l =
+1e-4, dx = W/2, 19-point Laplacian, no-flux box.  The state (3 x 64 MiB read
+and 3 x 64 MiB written per step) is larger than the 129 MB L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own independent 256^3 problem on its GPU
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle (the method as plainly written)
+on this host's cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2303_09671_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "phi/c_s/c_l cell-updates/s (3D 256^3 FP32)"
+UNIT = "cell-updates/s"
+PARAMS = dict(A=1.0, b=1.0)         # trapping parameter and normal-mobility shape
+
+
+def workload(n):
+    return wl.sphere_seed_3d(n=n, radius_cells=20.0, **PARAMS)
+
+
+def config(n, steps_note):
+    return {"workload": f"3D sphere seed {n}^3 FP32 (k_e=0.1, u=0.5, D_s/D_l=1e-4, dx=W/2, "
+                        f"19-pt, no-flux, A={PARAMS['A']}, b={PARAMS['b']})",
+            "grid": [n, n, n], "dtype": "f32", "cache": "state 201 MB > L2 (129 MB), no flush",
+            "scaling_unit": "one independent grid per rank", **steps_note}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n, max_seconds=25.0):
+    """Time the FP64 oracle on a bounded sample of the workload on the host cores."""
+    import oracle
+    pr, phi, cs, cl = workload(n)
+    st = oracle.State(pr, phi.astype(np.float32).astype(np.float64),
+                      cs.astype(np.float32).astype(np.float64), cl.astype(np.float32).astype(np.float64))
+    st.step(1)                               # warm-up (page-in, thread start)
+    cells = int(np.prod(pr["n"]))
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        st.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > max_seconds or steps >= 3:
+            break
+    return {"value": cells * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of the full {n}^3 grid after 1 warm-up step",
+            "seconds": el}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    n = args.size
+    pr, phi, cs, cl = workload(n)
+    st = oracle.State(pr, phi.astype(np.float32).astype(np.float64),
+                      cs.astype(np.float32).astype(np.float64), cl.astype(np.float32).astype(np.float64))
+    cells = int(np.prod(pr["n"]))
+    for _ in range(args.warmup):
+        st.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.step(1)
+    el = time.perf_counter() - t0
+    v = cells * args.steps / el
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config(n, {"arm": "FP64 CPU oracle, full grid per step"}),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"full {n}^3 grid, {args.steps} timed steps"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2303_09671_gb300.pf import Sim
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.size
+    pr, phi, cs, cl = workload(n)
+    cells = int(np.prod(pr["n"]))
+    f32 = [np.ascontiguousarray(a, dtype=np.float32) for a in (phi, cs, cl)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = Sim(pr, "fp32", stream=stream.cuda_stream)
+        sim.set_fields(*f32)
+        S0 = sim.solute_total()
+        for _ in range(args.warmup):
+            sim.step(1)
+        barrier()
+        stream.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                sim.step(1)
+            ev1.record(stream)
+            ev1.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        S1 = sim.solute_total()
+        drift = abs(S1 - S0) / abs(S0)
+
+        # end to end through the public API with host buffers: every step uploads
+        # the state from pinned host memory, steps, and reads back the solute total
+        pinned = [torch.from_numpy(a).pin_memory() for a in f32]
+        host_views = [p.numpy() for p in pinned]
+        ke = max(1, args.e2e_steps)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            sim.set_fields(*host_views)
+            sim.step(1)
+            sim.solute_total()
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        sim.close()
+
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+    value = cells * args.steps * world / (ms_max * 1e-3)
+    e2e_value = cells * ke * world / e2e_max
+
+    if rank == 0:
+        peak, how = load_peaks()
+        launch_s = ms / args.steps * 1e-3
+        bytes_per_launch = 24.0 * cells             # FP32 read + write of phi, c_s, c_l
+        achieved = bytes_per_launch / launch_s / 1e9
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config(n, {"parallelism": f"independent grid per GPU x{world}"}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": how,
+                         "kernel": "step_kernel<float,3,32,8>", "bytes_per_cell_update": 24},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * cells,
+                    "d2h_bytes_per_step": 16, "steps": ke},
+            "gpu_launches": args.steps,
+            "solute_drift": drift,
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(n)
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * pf.h -- C ABI of libpf: the explicit time step of the variational
+ * phase-field model of rapid alloy solidification of Mukherjee, Warren and
+ * Voorhees (arXiv 2303.09671) on uniform 1D/2D/3D grids, on one GB300 GPU.
+ *
+ * The model (all quantities in the scaled units length W, time W^2/D_l,
+ * concentration c0, energy density R T_m c0 / V_m):
+ *   fields: phase field phi (1 solid, 0 liquid) and the separately evolved
+ *   phase concentrations c_s, c_l (Sec. "Model", Eq. model1 with g = p);
+ *   phase-field rate: Eq. phasefield_nonvar with the driving force
+ *   DeltaG = f_s - f_l - mu_l (c_s - c_l) - D (c_s - c_l)(mu_s - mu_l),
+ *   D = [M_s (1-p)(1 - A(1-p)) + A b M_l p^2] / Mbar (re-derived from
+ *   Eq. model18 with the sources S_s = S_l = -A (c_s - c_l) of Sec.
+ *   "Asymptotic analysis"; the printed Eq. drivingforce_nonvar has a sign/b typo);
+ *   fluxes: the brackets of Eqs. cs_nonvar and cl_nonvar;
+ *   interpolation: p(phi) of Eq. interpolation2, h_n of Eq. interpolation1;
+ *   free energies: dilute ideal solution (Eqs. dil_linear, dil2, dil5) with
+ *   mobilities M_i = D_i c_i (supplement, non-dimensionalisation);
+ *   frozen temperature (Eq. ds1) and the moving window (Sec. "Numerical
+ *   technique"); explicit finite differences on a staggered grid, forward
+ *   Euler (Sec. "Numerical technique").
+ *
+ * Memory and ownership: a pf_handle owns every device buffer it allocates
+ * (two ping-pong copies of phi, c_s, c_l in the chosen precision, SoA, x
+ * fastest, plus reduction scratch).  Pointers passed to any call are borrowed
+ * for the duration of that call only.  All device work is ordered on the
+ * CUDA stream given to pf_create (a cudaStream_t passed as void*, NULL = the
+ * legacy default stream); calls that return host values synchronise that
+ * stream only.
+ *
+ * Errors: every int-returning call returns PF_OK (0) or a negative PF_E*
+ * code; pf_last_error() gives a message owned by the handle.  No exception
+ * and no abort crosses this boundary.
+ */
+#ifndef PF_H
+#define PF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PF_OK = 0,
+    PF_EINVAL = -1,        /* invalid argument or parameter */
+    PF_ENOMEM = -2,        /* device or host allocation failed */
+    PF_ECUDA = -3,         /* a CUDA runtime call failed */
+    PF_ENONFINITE = -4,    /* a non-finite value was found in the fields */
+    PF_ETIMEOUT = -5,      /* a bounded device wait ran out */
+    PF_EUNSUPPORTED = -6   /* combination not supported by this build */
+};
+enum { PF_BC_NOFLUX = 0, PF_BC_PERIODIC = 1, PF_BC_DIRICHLET = 2 };
+enum { PF_FP32 = 0, PF_FP64 = 1 };
+enum { PF_HOST = 0, PF_DEVICE = 1 };
+enum { PF_INTERP_QUINTIC = 0, PF_INTERP_CUBIC = 1 };  /* h(phi), Sec. "Choice of interpolation functions" */
+enum { PF_MOBILITY_DC = 0, PF_MOBILITY_CONST = 1 };   /* M_i = D_i c_i  or  M_i = D_i */
+
+/* Uniform grid: dim in {1,2,3}; n[a] cells along axis a (x = axis 0 is the
+ * fastest-varying index and the growth direction); unused axes must be 1;
+ * dx the spacing in units of W. */
+typedef struct {
+    int dim;
+    int64_t n[3];
+    double dx;
+} pf_grid;
+
+/* Boundary conditions per axis side (Sec. "Numerical technique"):
+ * PF_BC_NOFLUX   mirror ghosts and zero flux through the boundary face,
+ * PF_BC_PERIODIC wrap (both sides of the axis must be periodic),
+ * PF_BC_DIRICHLET fixed ghosts phi = dir_phi, c_s = dir_cs, c_l = dir_cl, whose
+ *                phase-field rate is zero.  The same values fill the fresh
+ *                layer of the moving window. */
+typedef struct {
+    int lo[3], hi[3];
+    double dir_phi, dir_cs, dir_cl;
+} pf_bc;
+
+/* Model and scheme parameters (scaled units).
+ *   precision      PF_FP32 or PF_FP64 field storage and arithmetic (the
+ *                  energy/solute reductions are always accumulated in FP64)
+ *   interp         PF_INTERP_QUINTIC or PF_INTERP_CUBIC h(phi)
+ *   lap_stencil    3 (1D), 5 or 9 (2D), 7 or 19 (3D) point Laplacian
+ *   mobility_mode  PF_MOBILITY_DC or PF_MOBILITY_CONST
+ *   H, sigma       well height and gradient coefficient (Eq. model1.1)
+ *   M_phi          phase-field mobility (Eq. model12)
+ *   D_s, D_l       phase diffusivities
+ *   k_e            equilibrium partition coefficient, 0 < k_e < 1 (Eq. dil2)
+ *   A              source/trapping parameter, S_s = S_l = -A (c_s - c_l)
+ *   b, a           interpolation parameters of Eqs. interpolation1/2 (b > 0)
+ *   delta          regularisation of 1/|grad phi|^2 -> 1/(|grad phi|^2 + delta^2)
+ *   theta_ref, G_theta, v_pull, x0
+ *                  frozen temperature in liquidus-concentration units,
+ *                  theta(x,t) = theta_ref - G_theta ((x - x0) - v_pull t)   (Eq. ds1)
+ *   dt             time step (must not exceed pf_stable_dt)
+ *   c_inf          alloy composition (fresh window layer and k_v = c_inf/c_max)
+ *   shift          1 = moving window along x (1D only): whenever v_pull t
+ *                  reaches the next multiple of dx, drop the cold-end cell
+ *                  and append a Dirichlet-valued cell at the hot end */
+typedef struct {
+    int precision;
+    int interp;
+    int lap_stencil;
+    int mobility_mode;
+    double H, sigma, M_phi, D_s, D_l, k_e, A, b, a, delta;
+    double theta_ref, G_theta, v_pull, x0, dt, c_inf;
+    int shift;
+} pf_params;
+
+typedef struct pf_handle pf_handle;
+
+/* Validate the problem, allocate the device state on `stream` and set the
+ * clock to step 0.  Fields are uninitialised until pf_set_fields.  Returns
+ * PF_EINVAL for: dim outside 1..3, n[a] < 3 on an active axis or != 1 on an
+ * inactive one, one-sided periodicity, dx <= 0, k_e outside (0,1), b <= 0,
+ * H, sigma, M_phi, D_s, D_l <= 0, a stencil that does not match dim,
+ * shift with dim != 1, dt <= 0 or dt above pf_stable_dt. */
+int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
+              void* stream, pf_handle** out);
+
+/* Copy the three fields in (pf_set_fields) or out (pf_get_fields).  Each
+ * pointer addresses n[0]*n[1]*n[2] values of the handle's precision (float or
+ * double), x fastest; where = PF_HOST (any host memory; pinned memory makes the
+ * copy asynchronous-capable) or PF_DEVICE.  pf_get_fields synchronises the
+ * stream. */
+int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where);
+int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
+
+/* Advance n >= 0 forward-Euler steps (stream-ordered, no host sync). */
+int pf_step(pf_handle* h, int64_t n);
+
+/* Discrete free energy of Eq. model1.1 for the current state, FP64:
+ *   F_h = dV sum_i [H f_dw(phi_i) + p_i f_s,i + (1-p_i) f_l,i]
+ *         + (sigma/2)(dV/dx^2) (1/2) sum_i sum_{j in stencil(i)} w_ij (phi_i - phi_j)^2,
+ * w_ij the Laplacian weights, ghosts from the boundary conditions.
+ * Synchronises the stream. */
+int pf_energy(pf_handle* h, double* F);
+
+/* Total solute S_h = dV sum_i [p_i c_s,i + (1-p_i) c_l,i] (Eq. model1), FP64.
+ * Synchronises the stream. */
+int pf_solute_total(pf_handle* h, double* S);
+
+/* Front diagnostics: x_front = largest phi = 0.5 crossing along x over all
+ * rows (linear interpolation, lab frame including window shifts; NaN when no
+ * row has a crossing); v_front = (x_front - previous x_front)/(t - previous t)
+ * from this handle's previous pf_front call (NaN on the first call or when no
+ * time has passed); c_max = max of c = p c_s + (1-p) c_l, so that
+ * k_v = c_inf / c_max (Sec. "Effect of parameter A on velocity-dependent
+ * partition coefficient").  Synchronises the stream. */
+int pf_front(pf_handle* h, double* x_front, double* v_front, double* c_max);
+
+/* Clock of the handle (steps taken, window shifts); with pf_get_fields and
+ * pf_set_fields this is a complete checkpoint. */
+int pf_get_clock(pf_handle* h, int64_t* step, int64_t* shifts);
+int pf_set_clock(pf_handle* h, int64_t step, int64_t shifts);
+
+/* Explicit-Euler step bound used by pf_create's check (the paper states
+ * none): min(dt_phi, dt_c) with lam = 4 dim / dx^2,
+ * dt_phi = 2 / (M_phi (lam sigma + 2 H)), dt_c = 2 / (lam D_max), D_max the
+ * largest concentration diffusivity q_n (p/c_s + (1-p)/c_l), M_s/c_s, M_l/c_l
+ * over p in [0,1] at c_s = k_e c_inf, c_l = c_inf. */
+int pf_stable_dt(const pf_grid* grid, const pf_params* params, double* dt);
+
+/* Message describing the last error on h (or the last pf_create failure when
+ * h is NULL).  Owned by the library; valid until the next call on h. */
+const char* pf_last_error(pf_handle* h);
+
+/* Free the handle and its device memory (stream-ordered). */
+void pf_destroy(pf_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

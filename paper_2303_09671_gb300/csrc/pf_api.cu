@@ -1,0 +1,330 @@
+// pf_api.cu -- the extern "C" boundary of libpf (declared in include/pf.h):
+// validation, device state, stream-ordered stepping and diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include "../../include/pf.h"
+#include "pf_kernels.h"
+
+struct pf_handle {
+    pf::HostProblem P;
+    cudaStream_t stream = nullptr;
+    void* buf[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int cur = 0;
+    int64_t step = 0, shifts = 0;
+    double* scratch = nullptr;   // diagnostics partials
+    double* dres = nullptr;      // device results (4 doubles)
+    double* hres = nullptr;      // pinned host results (4 doubles)
+    bool have_front = false;
+    double last_xf = 0.0, last_t = 0.0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(pf_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(pf_handle* h, cudaError_t e, const char* what) {
+    return fail(h, PF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+double effective_dmax(const pf_params* p) {
+    const double cs = p->k_e * p->c_inf, cl = p->c_inf;
+    const double Ms = (p->mobility_mode == PF_MOBILITY_CONST) ? p->D_s : p->D_s * cs;
+    const double Ml = (p->mobility_mode == PF_MOBILITY_CONST) ? p->D_l : p->D_l * cl;
+    double dmax = std::fmax(Ms / cs, Ml / cl);
+    const int S = 2001;
+    for (int i = 0; i < S; ++i) {
+        const double pp = (double)i / (S - 1);
+        const double Mbar = Ms * (1.0 - pp) + p->b * Ml * pp;
+        const double q = Ms * Ml * (p->b * pp + 1.0 - pp) / Mbar;
+        dmax = std::fmax(dmax, q * (pp / cs + (1.0 - pp) / cl));
+    }
+    return dmax;
+}
+
+double stable_dt(const pf_grid* g, const pf_params* p) {
+    const double lam = 4.0 * g->dim / (g->dx * g->dx);
+    const double dt_phi = 2.0 / (p->M_phi * (lam * p->sigma + 2.0 * p->H));
+    const double dt_c = 2.0 / (lam * effective_dmax(p));
+    return std::fmin(dt_phi, dt_c);
+}
+
+std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
+    if (!g || !bc || !p) return "null argument";
+    if (g->dim < 1 || g->dim > 3) return "dim must be 1, 2 or 3";
+    for (int a = 0; a < 3; ++a) {
+        if (a < g->dim) {
+            if (g->n[a] < 3) return "each active axis needs at least 3 cells";
+            const int lo = bc->lo[a], hi = bc->hi[a];
+            if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return "unknown boundary condition";
+            if ((lo == PF_BC_PERIODIC) != (hi == PF_BC_PERIODIC))
+                return "periodic boundaries must be set on both sides of an axis";
+        } else if (g->n[a] != 1) {
+            return "inactive axes must have n = 1";
+        }
+    }
+    if (g->n[0] > (1 << 30) || g->n[1] > (1 << 30) || g->n[2] > (1 << 30) ||
+        g->n[0] * g->n[1] * g->n[2] > (int64_t(1) << 34))
+        return "grid too large";
+    if (!(g->dx > 0)) return "dx must be positive";
+    if (p->precision != PF_FP32 && p->precision != PF_FP64) return "precision must be PF_FP32 or PF_FP64";
+    if (p->interp != PF_INTERP_QUINTIC && p->interp != PF_INTERP_CUBIC) return "unknown interp";
+    if (p->mobility_mode != PF_MOBILITY_DC && p->mobility_mode != PF_MOBILITY_CONST)
+        return "unknown mobility_mode";
+    const int L = p->lap_stencil;
+    if ((g->dim == 1 && L != 3) || (g->dim == 2 && L != 5 && L != 9) ||
+        (g->dim == 3 && L != 7 && L != 19))
+        return "lap_stencil must be 3 (1D), 5/9 (2D) or 7/19 (3D)";
+    if (!(p->H > 0) || !(p->sigma > 0) || !(p->M_phi > 0) || !(p->D_s > 0) || !(p->D_l > 0))
+        return "H, sigma, M_phi, D_s and D_l must be positive";
+    if (!(p->k_e > 0 && p->k_e < 1)) return "k_e must lie in (0, 1)";
+    if (!(p->b > 0)) return "b must be positive";
+    if (!(p->delta >= 0)) return "delta must be non-negative";
+    if (!(p->c_inf > 0)) return "c_inf must be positive";
+    if (!std::isfinite(p->A) || !std::isfinite(p->a) || !std::isfinite(p->theta_ref) ||
+        !std::isfinite(p->G_theta) || !std::isfinite(p->v_pull) || !std::isfinite(p->x0))
+        return "non-finite parameter";
+    if (p->shift && g->dim != 1) return "the moving window is supported in 1D only";
+    if (p->shift && !(p->v_pull * p->dt < g->dx)) return "v_pull dt must be below dx";
+    if (!(p->dt > 0)) return "dt must be positive";
+    const double dts = stable_dt(g, p);
+    if (p->dt > dts * (1.0 + 1e-12)) return "dt exceeds the explicit stability bound";
+    return "";
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pf_last_error(pf_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int pf_stable_dt(const pf_grid* grid, const pf_params* params, double* dt) {
+    if (!grid || !params || !dt) return fail(nullptr, PF_EINVAL, "null argument");
+    if (grid->dim < 1 || grid->dim > 3 || !(grid->dx > 0) || !(params->M_phi > 0) ||
+        !(params->k_e > 0 && params->k_e < 1) || !(params->b > 0) || !(params->c_inf > 0))
+        return fail(nullptr, PF_EINVAL, "invalid grid or parameters");
+    *dt = stable_dt(grid, params);
+    return PF_OK;
+}
+
+int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, void* stream,
+              pf_handle** out) {
+    if (!out) return fail(nullptr, PF_EINVAL, "null output pointer");
+    *out = nullptr;
+    const std::string why = validate(grid, bc, params);
+    if (!why.empty()) return fail(nullptr, PF_EINVAL, why);
+    pf_handle* h = new (std::nothrow) pf_handle();
+    if (!h) return fail(nullptr, PF_ENOMEM, "host allocation failed");
+    pf::HostProblem& P = h->P;
+    P.dim = grid->dim;
+    for (int a = 0; a < 3; ++a) {
+        P.n[a] = grid->n[a];
+        P.bc_lo[a] = (a < grid->dim) ? bc->lo[a] : PF_BC_NOFLUX;
+        P.bc_hi[a] = (a < grid->dim) ? bc->hi[a] : PF_BC_NOFLUX;
+    }
+    P.dx = grid->dx;
+    P.dir_phi = bc->dir_phi; P.dir_cs = bc->dir_cs; P.dir_cl = bc->dir_cl;
+    P.precision = params->precision;
+    P.interp = params->interp;
+    P.lap = params->lap_stencil;
+    P.mobility = params->mobility_mode;
+    P.H = params->H; P.sigma = params->sigma; P.M_phi = params->M_phi;
+    P.D_s = params->D_s; P.D_l = params->D_l; P.k_e = params->k_e;
+    P.A = params->A; P.b = params->b; P.a = params->a; P.delta = params->delta;
+    P.theta_ref = params->theta_ref; P.G_theta = params->G_theta;
+    P.v_pull = params->v_pull; P.x0 = params->x0; P.dt = params->dt; P.c_inf = params->c_inf;
+    P.shift = params->shift ? 1 : 0;
+    h->stream = static_cast<cudaStream_t>(stream);
+
+    const size_t bytes = (size_t)P.cells() * P.elem();
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 3; ++f) {
+            cudaError_t e = cudaMalloc(&h->buf[b][f], bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                pf_destroy(h);
+                return fail(nullptr, PF_ENOMEM, std::string("device allocation failed: ") +
+                                                    cudaGetErrorString(e));
+            }
+        }
+    cudaError_t e = cudaMalloc(&h->scratch, pf::diag_scratch_doubles(P) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dres, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->hres, 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        pf_destroy(h);
+        return fail(nullptr, PF_ENOMEM, std::string("allocation failed: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return PF_OK;
+}
+
+void pf_destroy(pf_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 3; ++f)
+            if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->dres) cudaFree(h->dres);
+    if (h->hres) cudaFreeHost(h->hres);
+    delete h;
+}
+
+static int copy_fields(pf_handle* h, void* const dst[3], const void* const src[3], cudaMemcpyKind k) {
+    const size_t bytes = (size_t)h->P.cells() * h->P.elem();
+    for (int f = 0; f < 3; ++f) {
+        cudaError_t e = cudaMemcpyAsync(dst[f], src[f], bytes, k, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+    }
+    return PF_OK;
+}
+
+int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    void* dst[3] = {h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2]};
+    const void* src[3] = {phi, cs, cl};
+    int rc = copy_fields(h, dst, src, where == PF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
+    if (rc) return rc;
+    h->have_front = false;
+    if (where == PF_HOST) {
+        // the caller may reuse pageable host memory as soon as we return
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+    return PF_OK;
+}
+
+int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    void* dst[3] = {phi, cs, cl};
+    const void* src[3] = {h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2]};
+    int rc = copy_fields(h, dst, src, where == PF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return PF_OK;
+}
+
+int pf_step(pf_handle* h, int64_t n) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (n < 0) return fail(h, PF_EINVAL, "negative step count");
+    const pf::HostProblem& P = h->P;
+    for (int64_t s = 0; s < n; ++s) {
+        pf::StepLaunch a;
+        a.prob = &P;
+        a.phi_in = h->buf[h->cur][0]; a.cs_in = h->buf[h->cur][1]; a.cl_in = h->buf[h->cur][2];
+        a.phi_out = h->buf[h->cur ^ 1][0]; a.cs_out = h->buf[h->cur ^ 1][1]; a.cl_out = h->buf[h->cur ^ 1][2];
+        a.step = h->step;
+        a.shifts = h->shifts;
+        a.zchunk = 0;
+        a.stream = h->stream;
+        cudaError_t e = pf::launch_step(a);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+        h->cur ^= 1;
+        h->step += 1;
+        if (P.shift) {
+            const double t = (double)h->step * P.dt;
+            while (P.v_pull * t >= (double)(h->shifts + 1) * P.dx) {
+                e = pf::launch_shift(P, h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2],
+                                     h->buf[h->cur ^ 1][0], h->buf[h->cur ^ 1][1],
+                                     h->buf[h->cur ^ 1][2], h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "shift kernel launch");
+                h->cur ^= 1;
+                h->shifts += 1;
+            }
+        }
+    }
+    return PF_OK;
+}
+
+static int fetch_results(pf_handle* h, int count) {
+    cudaError_t e = cudaMemcpyAsync(h->hres, h->dres, count * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "result copy");
+    return PF_OK;
+}
+
+static int energy_solute(pf_handle* h) {
+    cudaError_t e = pf::launch_energy_solute(h->P, h->buf[h->cur][0], h->buf[h->cur][1],
+                                             h->buf[h->cur][2], h->step, h->shifts, h->scratch,
+                                             h->dres, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy kernel launch");
+    return fetch_results(h, 2);
+}
+
+int pf_energy(pf_handle* h, double* F) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!F) return fail(h, PF_EINVAL, "null output");
+    int rc = energy_solute(h);
+    if (rc) return rc;
+    *F = h->hres[0];
+    if (!std::isfinite(*F)) return fail(h, PF_ENONFINITE, "non-finite free energy");
+    return PF_OK;
+}
+
+int pf_solute_total(pf_handle* h, double* S) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!S) return fail(h, PF_EINVAL, "null output");
+    int rc = energy_solute(h);
+    if (rc) return rc;
+    *S = h->hres[1];
+    if (!std::isfinite(*S)) return fail(h, PF_ENONFINITE, "non-finite solute total");
+    return PF_OK;
+}
+
+int pf_front(pf_handle* h, double* x_front, double* v_front, double* c_max) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!x_front || !v_front || !c_max) return fail(h, PF_EINVAL, "null output");
+    cudaError_t e = pf::launch_front(h->P, h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2],
+                                     h->scratch, h->dres, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "front kernel launch");
+    int rc = fetch_results(h, 2);
+    if (rc) return rc;
+    const double xf = h->hres[0] + (double)h->shifts * h->P.dx;
+    const double t = (double)h->step * h->P.dt;
+    *x_front = xf;
+    *c_max = h->hres[1];
+    *v_front = (h->have_front && t > h->last_t) ? (xf - h->last_xf) / (t - h->last_t) : NAN;
+    h->have_front = true;
+    h->last_xf = xf;
+    h->last_t = t;
+    if (!std::isfinite(*c_max)) return fail(h, PF_ENONFINITE, "non-finite concentration");
+    return PF_OK;
+}
+
+int pf_get_clock(pf_handle* h, int64_t* step, int64_t* shifts) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!step || !shifts) return fail(h, PF_EINVAL, "null output");
+    *step = h->step;
+    *shifts = h->shifts;
+    return PF_OK;
+}
+
+int pf_set_clock(pf_handle* h, int64_t step, int64_t shifts) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (step < 0 || shifts < 0) return fail(h, PF_EINVAL, "negative clock");
+    h->step = step;
+    h->shifts = shifts;
+    h->have_front = false;
+    return PF_OK;
+}
+
+}  // extern "C"

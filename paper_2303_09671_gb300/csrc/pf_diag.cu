@@ -1,0 +1,268 @@
+// pf_diag.cu -- FP64 diagnostics (discrete free energy, total solute, front,
+// c_max), the 1D moving-window shift and a non-finite check.
+//
+// Reductions are deterministic: a fixed grid of DIAG_BLOCKS blocks writes one
+// partial per block (warp-shuffle tree inside the block), and a single block
+// sums the partials in a fixed order.
+#include <cmath>
+#include <cstdint>
+#include "pf_internal.cuh"
+#include "pf_kernels.h"
+
+namespace pf {
+
+static constexpr int DIAG_THREADS = 256;
+static constexpr int DIAG_BLOCKS = 1216;   // 8 per SM on a 152-SM GB300
+
+size_t diag_scratch_doubles(const HostProblem&) { return 2 * (size_t)DIAG_BLOCKS; }
+
+struct DiagConsts {
+    int n[3], bc_lo[3], bc_hi[3], dim, lap, interp;
+    double dir_phi, dx, H, sigma, k_e, a, theta0, G_theta, dV;
+};
+
+__device__ __forceinline__ double p_d(const DiagConsts& C, double f) {
+    double g = f * (1.0 - f);
+    double h = (C.interp == 1) ? f * f * (3.0 - 2.0 * f) : f * f * f * (6.0 * f * f - 15.0 * f + 10.0);
+    return h + C.a * (f - 0.5) * g * g;
+}
+
+template <typename T>
+__device__ __forceinline__ double fetch_phi(const DiagConsts& C, const T* phi, int i, int j, int k) {
+    int mi = map_coord(i, C.n[0], C.bc_lo[0], C.bc_hi[0]);
+    int mj = (C.dim >= 2) ? map_coord(j, C.n[1], C.bc_lo[1], C.bc_hi[1]) : 0;
+    int mk = (C.dim >= 3) ? map_coord(k, C.n[2], C.bc_lo[2], C.bc_hi[2]) : 0;
+    if (mi < 0 || mj < 0 || mk < 0) return C.dir_phi;
+    return (double)phi[((long long)mk * C.n[1] + mj) * C.n[0] + mi];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// block reduction of two values (sum or max), result valid in thread 0
+template <bool MAX>
+__device__ void block_reduce2(double& a, double& b) {
+    __shared__ double sa[DIAG_THREADS / 32], sb[DIAG_THREADS / 32];
+    a = MAX ? warp_max(a) : warp_sum(a);
+    b = MAX ? warp_max(b) : warp_sum(b);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    if (l == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = (l < DIAG_THREADS / 32) ? sa[l] : (MAX ? -INFINITY : 0.0);
+        b = (l < DIAG_THREADS / 32) ? sb[l] : (MAX ? -INFINITY : 0.0);
+        a = MAX ? warp_max(a) : warp_sum(a);
+        b = MAX ? warp_max(b) : warp_sum(b);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS)
+energy_solute_kernel(const T* __restrict__ phi, const T* __restrict__ cs,
+                     const T* __restrict__ cl, DiagConsts C, double* __restrict__ part) {
+    const long long N = (long long)C.n[0] * C.n[1] * C.n[2];
+    // Laplacian stencil weights (units of 1/dx^2), centre excluded
+    double eF = 0.0, eS = 0.0;
+    const double one_m_ke = 1.0 - C.k_e, log_ke = log(C.k_e);
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % C.n[0]);
+        const int j = (int)((c / C.n[0]) % C.n[1]);
+        const int k = (int)(c / ((long long)C.n[0] * C.n[1]));
+        const double f = (double)phi[c], s = (double)cs[c], l = (double)cl[c];
+        const double p = p_d(C, f);
+        const double theta = C.theta0 - C.G_theta * (((double)i + 0.5) * C.dx);
+        const double fs = -one_m_ke * theta + s * (log(s) - log_ke - 1.0);
+        const double fl = l * (log(l) - 1.0);
+        const double fdw = f * f * (1.0 - f) * (1.0 - f);
+        double gs = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int nzc = (dx != 0) + (dy != 0) + (dz != 0);
+                    if (nzc == 0) continue;
+                    double w = 0.0;
+                    if (C.lap == 3) w = (dy == 0 && dz == 0) ? 1.0 : 0.0;
+                    else if (C.lap == 5) w = (dz == 0 && nzc == 1) ? 1.0 : 0.0;
+                    else if (C.lap == 9) w = (dz != 0) ? 0.0 : (nzc == 1 ? 2.0 / 3.0 : 1.0 / 6.0);
+                    else if (C.lap == 7) w = (nzc == 1) ? 1.0 : 0.0;
+                    else w = (nzc == 1) ? 1.0 / 3.0 : (nzc == 2 ? 1.0 / 6.0 : 0.0);
+                    if (w == 0.0) continue;
+                    const double dphi = fetch_phi(C, phi, i + dx, j + dy, k + dz) - f;
+                    gs += w * dphi * dphi;
+                }
+        eF += C.H * fdw + p * fs + (1.0 - p) * fl + 0.5 * C.sigma * 0.5 * gs / (C.dx * C.dx);
+        eS += p * s + (1.0 - p) * l;
+    }
+    block_reduce2<false>(eF, eS);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = eF;
+        part[gridDim.x + blockIdx.x] = eS;
+    }
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+finish_sum2(const double* __restrict__ part, int nb, double scale, double* __restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += part[i];
+        b += part[nb + i];
+    }
+    block_reduce2<false>(a, b);
+    if (threadIdx.x == 0) {
+        out[0] = a * scale;
+        out[1] = b * scale;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS)
+front_kernel(const T* __restrict__ phi, const T* __restrict__ cs, const T* __restrict__ cl,
+             DiagConsts C, double* __restrict__ part) {
+    const long long rows = (long long)C.n[1] * C.n[2];
+    double xf = -INFINITY, cm = -INFINITY;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+         r += (long long)gridDim.x * blockDim.x) {
+        const T* prow = phi + r * C.n[0];
+        for (int i = C.n[0] - 2; i >= 0; --i) {
+            const double a = (double)prow[i], b = (double)prow[i + 1];
+            if (a >= 0.5 && b < 0.5) {
+                xf = fmax(xf, ((double)i + 0.5 + (a - 0.5) / (a - b)) * C.dx);
+                break;
+            }
+        }
+        for (int i = 0; i < C.n[0]; ++i) {
+            const double p = p_d(C, (double)prow[i]);
+            cm = fmax(cm, p * (double)cs[r * C.n[0] + i] + (1.0 - p) * (double)cl[r * C.n[0] + i]);
+        }
+    }
+    block_reduce2<true>(xf, cm);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = xf;
+        part[gridDim.x + blockIdx.x] = cm;
+    }
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+finish_max2(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    double a = -INFINITY, b = -INFINITY;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a = fmax(a, part[i]);
+        b = fmax(b, part[nb + i]);
+    }
+    block_reduce2<true>(a, b);
+    if (threadIdx.x == 0) {
+        out[0] = (a == -INFINITY) ? NAN : a;
+        out[1] = b;
+    }
+}
+
+template <typename T>
+__global__ void shift_kernel(const T* __restrict__ pi, const T* __restrict__ si,
+                             const T* __restrict__ li, T* __restrict__ po, T* __restrict__ so,
+                             T* __restrict__ lo, int n, T fp, T fs, T fl) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < n - 1) {
+            po[i] = pi[i + 1]; so[i] = si[i + 1]; lo[i] = li[i + 1];
+        } else {
+            po[i] = fp; so[i] = fs; lo[i] = fl;
+        }
+    }
+}
+
+template <typename T>
+__global__ void finite_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                              const T* __restrict__ c, long long n, int* flag) {
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[i]) | !isfinite(b[i]) | !isfinite(c[i]);
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+static DiagConsts make_diag(const HostProblem& P, int64_t step, int64_t shifts) {
+    DiagConsts C;
+    for (int a = 0; a < 3; ++a) {
+        C.n[a] = (int)P.n[a];
+        C.bc_lo[a] = P.bc_lo[a];
+        C.bc_hi[a] = P.bc_hi[a];
+    }
+    C.dim = P.dim;
+    C.lap = P.lap;
+    C.interp = P.interp;
+    C.dir_phi = P.dir_phi;
+    C.dx = P.dx;
+    C.H = P.H;
+    C.sigma = P.sigma;
+    C.k_e = P.k_e;
+    C.a = P.a;
+    const double t = (double)step * P.dt;
+    C.theta0 = P.theta_ref + P.G_theta * (P.x0 + P.v_pull * t - (double)shifts * P.dx);
+    C.G_theta = P.G_theta;
+    C.dV = std::pow(P.dx, P.dim);
+    return C;
+}
+
+cudaError_t launch_energy_solute(const HostProblem& P, const void* phi, const void* cs,
+                                 const void* cl, int64_t step, int64_t shifts,
+                                 double* scratch, double* out, cudaStream_t s) {
+    const DiagConsts C = make_diag(P, step, shifts);
+    if (P.precision == 1)
+        energy_solute_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const double*)phi, (const double*)cs, (const double*)cl, C, scratch);
+    else
+        energy_solute_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const float*)phi, (const float*)cs, (const float*)cl, C, scratch);
+    finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, C.dV, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_front(const HostProblem& P, const void* phi, const void* cs,
+                         const void* cl, double* scratch, double* out, cudaStream_t s) {
+    const DiagConsts C = make_diag(P, 0, 0);
+    if (P.precision == 1)
+        front_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const double*)phi, (const double*)cs, (const double*)cl, C, scratch);
+    else
+        front_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const float*)phi, (const float*)cs, (const float*)cl, C, scratch);
+    finish_max2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift(const HostProblem& P, const void* pi, const void* si, const void* li,
+                         void* po, void* so, void* lo, cudaStream_t s) {
+    const int n = (int)P.n[0];
+    const int blocks = (n + 255) / 256;
+    if (P.precision == 1)
+        shift_kernel<double><<<blocks, 256, 0, s>>>((const double*)pi, (const double*)si,
+                                                    (const double*)li, (double*)po, (double*)so,
+                                                    (double*)lo, n, P.dir_phi, P.dir_cs, P.dir_cl);
+    else
+        shift_kernel<float><<<blocks, 256, 0, s>>>((const float*)pi, (const float*)si,
+                                                   (const float*)li, (float*)po, (float*)so,
+                                                   (float*)lo, n, (float)P.dir_phi,
+                                                   (float)P.dir_cs, (float)P.dir_cl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finite_check(const HostProblem& P, const void* phi, const void* cs,
+                                const void* cl, int* flag, cudaStream_t s) {
+    const long long n = P.cells();
+    if (P.precision == 1)
+        finite_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const double*)phi, (const double*)cs, (const double*)cl, n, flag);
+    else
+        finite_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const float*)phi, (const float*)cs, (const float*)cl, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,57 @@
+// pf_kernels.h -- host-side launch interface between the C ABI (pf_api.cu)
+// and the kernels (pf_step.cu, pf_diag.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cmath>
+#include <cuda_runtime.h>
+
+namespace pf {
+
+// Validated problem description, host copy (FP64 parameters).
+struct HostProblem {
+    int dim;
+    int64_t n[3];
+    double dx;
+    int bc_lo[3], bc_hi[3];
+    double dir_phi, dir_cs, dir_cl;
+    int precision;   // 0 FP32, 1 FP64
+    int interp, lap, mobility;
+    double H, sigma, M_phi, D_s, D_l, k_e, A, b, a, delta;
+    double theta_ref, G_theta, v_pull, x0, dt, c_inf;
+    int shift;
+    int64_t cells() const { return n[0] * n[1] * n[2]; }
+    size_t elem() const { return precision == 1 ? sizeof(double) : sizeof(float); }
+};
+
+struct StepLaunch {
+    const HostProblem* prob;
+    const void *phi_in, *cs_in, *cl_in;
+    void *phi_out, *cs_out, *cl_out;
+    int64_t step, shifts;   // clock of the input state
+    int zchunk;             // planes per CTA along z (3D); <= 0: whole column
+    cudaStream_t stream;
+};
+
+cudaError_t launch_step(const StepLaunch& a);
+size_t step_smem_bytes(int precision, int dim);
+
+// Diagnostics.  `scratch` must hold diag_scratch_doubles(prob) doubles; results
+// are written as doubles to out (device pointer):
+//   energy_solute: out[0] = F_h, out[1] = S_h
+//   front:         out[0] = x_front (local, without the window offset; NaN if
+//                  none), out[1] = c_max
+size_t diag_scratch_doubles(const HostProblem& P);
+cudaError_t launch_energy_solute(const HostProblem& P, const void* phi, const void* cs,
+                                 const void* cl, int64_t step, int64_t shifts,
+                                 double* scratch, double* out, cudaStream_t s);
+cudaError_t launch_front(const HostProblem& P, const void* phi, const void* cs,
+                         const void* cl, double* scratch, double* out, cudaStream_t s);
+// moving window: out[i] = in[i+1] (i < n-1), out[n-1] = fresh value (1D)
+cudaError_t launch_shift(const HostProblem& P, const void* phi_in, const void* cs_in,
+                         const void* cl_in, void* phi_out, void* cs_out, void* cl_out,
+                         cudaStream_t s);
+// non-finite check: *flag (device int) set to 1 if any value is not finite
+cudaError_t launch_finite_check(const HostProblem& P, const void* phi, const void* cs,
+                                const void* cl, int* flag, cudaStream_t s);
+
+}  // namespace pf

@@ -1,0 +1,225 @@
+"""Python binding of libpf (include/pf.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of libpf.so; there is no CPU
+fallback.  If the library cannot be built or loaded, or no GPU is present,
+the calls raise.
+
+Parameters use the dict produced by ``workloads.scaled_params``.  Host arrays
+are numpy arrays; device arrays are torch CUDA tensors (passed by data_ptr).
+By default the handle runs on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ETIMEOUT, PF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+PF_HOST, PF_DEVICE = 0, 1
+BC = {"noflux": 0, "periodic": 1, "dirichlet": 2}
+PRECISION = {"fp32": 0, "fp64": 1}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libpf error {code}: {msg}")
+        self.code = code
+
+
+class pf_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double)]
+
+
+class pf_bc(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3), ("dir_phi", ctypes.c_double),
+                ("dir_cs", ctypes.c_double), ("dir_cl", ctypes.c_double)]
+
+
+class pf_params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("interp", ctypes.c_int), ("lap_stencil", ctypes.c_int),
+                ("mobility_mode", ctypes.c_int)] + [
+        (k, ctypes.c_double) for k in ("H", "sigma", "M_phi", "D_s", "D_l", "k_e", "A", "b", "a",
+                                       "delta", "theta_ref", "G_theta", "v_pull", "x0", "dt", "c_inf")
+    ] + [("shift", ctypes.c_int)]
+
+
+# exported symbols and their signatures (the header include/pf.h declares the same set)
+_VP = ctypes.c_void_p
+_SIGS = {
+    "pf_create": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_bc),
+                                 ctypes.POINTER(pf_params), _VP, ctypes.POINTER(_VP)]),
+    "pf_set_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "pf_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "pf_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "pf_energy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "pf_solute_total": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "pf_front": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_double)] * 3),
+    "pf_get_clock": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "pf_set_clock": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64]),
+    "pf_stable_dt": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_params),
+                                    ctypes.POINTER(ctypes.c_double)]),
+    "pf_last_error": (ctypes.c_char_p, [_VP]),
+    "pf_destroy": (None, [_VP]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpf.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, h=None):
+    if rc != PF_OK:
+        msg = lib().pf_last_error(h)
+        raise PFError(rc, msg.decode() if msg else "")
+
+
+def make_structs(pr: dict, precision: str = "fp32"):
+    g = pf_grid()
+    g.dim = int(pr["dim"])
+    n = list(pr["n"]) + [1] * (3 - len(pr["n"]))
+    for a in range(3):
+        g.n[a] = int(n[a])
+    g.dx = float(pr["dx"])
+    b = pf_bc()
+    for a in range(3):
+        b.lo[a] = BC[pr["bc_lo"][a]] if a < g.dim else 0
+        b.hi[a] = BC[pr["bc_hi"][a]] if a < g.dim else 0
+    b.dir_phi, b.dir_cs, b.dir_cl = (float(v) for v in pr.get("dirichlet", (0.0, 0.0, 1.0)))
+    p = pf_params()
+    p.precision = PRECISION[precision]
+    p.interp = {"quintic": 0, "cubic": 1}[pr.get("interp", "quintic")]
+    p.lap_stencil = int(pr["lap"])
+    p.mobility_mode = {"Dc": 0, "const": 1}[pr.get("mobility", "Dc")]
+    for k in ("H", "sigma", "M_phi", "D_s", "D_l", "k_e", "A", "b", "a", "delta", "theta_ref",
+              "G_theta", "v_pull", "x0", "dt", "c_inf"):
+        setattr(p, k, float(pr[k]))
+    p.shift = int(bool(pr.get("shift", False)))
+    if pr.get("form", "cd") != "cd":
+        raise ValueError("libpf implements the conservative (c, d) update only")
+    return g, b, p
+
+
+def stable_dt(pr: dict) -> float:
+    g, _, p = make_structs(pr)
+    out = ctypes.c_double()
+    _check(lib().pf_stable_dt(ctypes.byref(g), ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+def _current_stream():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libpf needs a CUDA device")
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Sim:
+    """One simulation handle (pf_create ... pf_destroy)."""
+
+    def __init__(self, pr: dict, precision: str = "fp32", stream=None):
+        self.pr = dict(pr)
+        self.precision = precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.shape = tuple(int(v) for v in list(pr["n"])[: pr["dim"]][::-1])
+        g, b, p = make_structs(pr, precision)
+        s = _current_stream() if stream is None else stream
+        h = _VP()
+        rc = lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), _VP(s), ctypes.byref(h))
+        _check(rc, None)
+        self._h = h
+        self.stream = s
+
+    # -- fields
+    def set_fields(self, phi, cs, cl):
+        if all(hasattr(a, "data_ptr") for a in (phi, cs, cl)):
+            for a in (phi, cs, cl):
+                if not a.is_cuda or not a.is_contiguous() or tuple(a.shape) != self.shape:
+                    raise ValueError("device fields must be contiguous CUDA tensors of the grid shape")
+                if a.element_size() != np.dtype(self.dtype).itemsize:
+                    raise ValueError("device field dtype does not match the handle precision")
+            ptrs = [_VP(a.data_ptr()) for a in (phi, cs, cl)]
+            _check(lib().pf_set_fields(self._h, *ptrs, PF_DEVICE), self._h)
+            return
+        arrs = [np.ascontiguousarray(a, dtype=self.dtype) for a in (phi, cs, cl)]
+        for a in arrs:
+            if a.shape != self.shape:
+                raise ValueError(f"field shape {a.shape} != {self.shape}")
+        _check(lib().pf_set_fields(self._h, *[_VP(a.ctypes.data) for a in arrs], PF_HOST), self._h)
+
+    def get_fields(self, out=None):
+        """Return (phi, cs, cl) as numpy arrays, or fill the given CUDA tensors."""
+        if out is not None:
+            ptrs = [_VP(a.data_ptr()) for a in out]
+            _check(lib().pf_get_fields(self._h, *ptrs, PF_DEVICE), self._h)
+            return out
+        arrs = [np.empty(self.shape, dtype=self.dtype) for _ in range(3)]
+        _check(lib().pf_get_fields(self._h, *[_VP(a.ctypes.data) for a in arrs], PF_HOST), self._h)
+        return tuple(arrs)
+
+    # -- stepping and diagnostics
+    def step(self, n: int = 1):
+        _check(lib().pf_step(self._h, int(n)), self._h)
+
+    def energy(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().pf_energy(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def solute_total(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().pf_solute_total(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def front(self):
+        x, v, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().pf_front(self._h, ctypes.byref(x), ctypes.byref(v), ctypes.byref(c)), self._h)
+        return x.value, v.value, c.value
+
+    @property
+    def clock(self):
+        s, k = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pf_get_clock(self._h, ctypes.byref(s), ctypes.byref(k)), self._h)
+        return s.value, k.value
+
+    def set_clock(self, step: int, shifts: int = 0):
+        _check(lib().pf_set_clock(self._h, int(step), int(shifts)), self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

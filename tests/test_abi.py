@@ -1,0 +1,87 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/pf.h declares, validates its arguments before touching the
+device, and its stable-dt rule agrees with the input recipe's."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2303_09671_gb300 import build as pbuild
+from paper_2303_09671_gb300 import pf
+from paper_2303_09671_gb300 import workloads as wl
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "pf.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", src)))
+
+
+def test_library_loads_and_exports_header_symbols():
+    L = pf.lib()
+    names = declared_functions()
+    assert "pf_create" in names and "pf_step" in names
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in pf.h but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", pbuild.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pf_[a-z_]+)\b", out))
+    assert set(names) == exported, f"header/exports mismatch: {set(names) ^ exported}"
+
+
+def test_binding_covers_header():
+    assert set(pf._SIGS) == set(declared_functions())
+
+
+def _create(pr, **over):
+    g, b, p = pf.make_structs(pr, "fp32")
+    for k, v in over.items():
+        for s in (g, b, p):
+            if hasattr(s, k):
+                setattr(s, k, v)
+    h = ctypes.c_void_p()
+    rc = pf.lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), None, ctypes.byref(h))
+    return rc, pf.lib().pf_last_error(None).decode()
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(dim=4), "dim"),
+    (dict(k_e=1.5), "k_e"),
+    (dict(b=0.0), "b must"),
+    (dict(lap_stencil=5), "lap_stencil"),
+    (dict(dt=1.0), "stability"),
+    (dict(dx=-1.0), "dx"),
+    (dict(M_phi=0.0), "positive"),
+    (dict(shift=1), "1D only"),
+])
+def test_create_rejects_invalid(over, needle):
+    pr, *_ = wl.random_state(3, (16, 8, 8))
+    rc, msg = _create(pr, **over)
+    assert rc == pf.PF_EINVAL and needle in msg
+
+
+def test_create_rejects_one_sided_periodic():
+    pr, *_ = wl.random_state(2, (16, 8), bc_lo=("periodic", "noflux"), bc_hi=("noflux", "noflux"))
+    rc, msg = _create(pr)
+    assert rc == pf.PF_EINVAL and "periodic" in msg
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = pf.lib()
+    assert L.pf_step(None, 1) == pf.PF_EINVAL
+    v = ctypes.c_double()
+    assert L.pf_energy(None, ctypes.byref(v)) == pf.PF_EINVAL
+    L.pf_destroy(None)
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: wl.planar_1d(A=2.0, b=1.0),
+    lambda: wl.perturbed_front_2d(nx=64, ny=64, A=1.5, b=0.3),
+    lambda: wl.random_state(3, (16, 8, 8), mobility="const"),
+])
+def test_stable_dt_matches_recipe(maker):
+    pr = maker()[0]
+    assert abs(pf.stable_dt(pr) - wl.stable_dt(pr)) <= 1e-13 * wl.stable_dt(pr)
