@@ -18,8 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpf.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# --prec-div=false: FP32 divisions use the approximate reciprocal (FP64 is unaffected)
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-           "-Xptxas", "-warn-spills"]
+           "--prec-div=false", "-Xptxas", "-warn-spills"]
 
 
 def nvcc() -> str:

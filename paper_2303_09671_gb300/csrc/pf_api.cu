@@ -2,6 +2,7 @@
 // validation, device state, stream-ordered stepping and diagnostics.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -11,12 +12,13 @@
 struct pf_handle {
     pf::HostProblem P;
     cudaStream_t stream = nullptr;
-    void* buf[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    pf::Fields buf[2] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
     int cur = 0;
     int64_t step = 0, shifts = 0;
     double* scratch = nullptr;   // diagnostics partials
     double* dres = nullptr;      // device results (4 doubles)
     double* hres = nullptr;      // pinned host results (4 doubles)
+    int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
     bool have_front = false;
     double last_xf = 0.0, last_t = 0.0;
     std::string err;
@@ -146,11 +148,14 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     P.v_pull = params->v_pull; P.x0 = params->x0; P.dt = params->dt; P.c_inf = params->c_inf;
     P.shift = params->shift ? 1 : 0;
     h->stream = static_cast<cudaStream_t>(stream);
+    if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
 
     const size_t bytes = (size_t)P.cells() * P.elem();
-    for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < 3; ++f) {
-            cudaError_t e = cudaMalloc(&h->buf[b][f], bytes);
+    for (int b = 0; b < 2; ++b) {
+        void** slots[4] = {&h->buf[b].phi, &h->buf[b].c, &h->buf[b].d, &h->buf[b].clo};
+        const int nf = (P.precision == PF_FP32) ? 4 : 3;   // FP32 keeps the low word of c
+        for (int f = 0; f < nf; ++f) {
+            cudaError_t e = cudaMalloc(slots[f], bytes);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 pf_destroy(h);
@@ -158,6 +163,7 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
                                                     cudaGetErrorString(e));
             }
         }
+    }
     cudaError_t e = cudaMalloc(&h->scratch, pf::diag_scratch_doubles(P) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->dres, 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&h->hres, 4 * sizeof(double));
@@ -174,36 +180,39 @@ void pf_destroy(pf_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < 3; ++f)
-            if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+    for (int b = 0; b < 2; ++b) {
+        void* slots[4] = {h->buf[b].phi, h->buf[b].c, h->buf[b].d, h->buf[b].clo};
+        for (void* p : slots)
+            if (p) cudaFree(p);
+    }
     if (h->scratch) cudaFree(h->scratch);
     if (h->dres) cudaFree(h->dres);
     if (h->hres) cudaFreeHost(h->hres);
     delete h;
 }
 
-static int copy_fields(pf_handle* h, void* const dst[3], const void* const src[3], cudaMemcpyKind k) {
-    const size_t bytes = (size_t)h->P.cells() * h->P.elem();
-    for (int f = 0; f < 3; ++f) {
-        cudaError_t e = cudaMemcpyAsync(dst[f], src[f], bytes, k, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
-    }
-    return PF_OK;
-}
-
 int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
-    void* dst[3] = {h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2]};
+    const size_t bytes = (size_t)h->P.cells() * h->P.elem();
     const void* src[3] = {phi, cs, cl};
-    int rc = copy_fields(h, dst, src, where == PF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
-    if (rc) return rc;
+    if (where == PF_HOST) {
+        // stage (phi, c_s, c_l) in the idle ping-pong buffer, then convert
+        const pf::Fields& st = h->buf[h->cur ^ 1];
+        void* dst[3] = {st.phi, st.c, st.d};
+        for (int f = 0; f < 3; ++f) {
+            cudaError_t e = cudaMemcpyAsync(dst[f], src[f], bytes, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+        }
+        for (int f = 0; f < 3; ++f) src[f] = dst[f];
+    }
+    cudaError_t e = pf::launch_to_state(h->P, src[0], src[1], src[2], h->buf[h->cur], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
     h->have_front = false;
     if (where == PF_HOST) {
         // the caller may reuse pageable host memory as soon as we return
-        cudaError_t e = cudaStreamSynchronize(h->stream);
+        e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     }
     return PF_OK;
@@ -213,11 +222,22 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
-    void* dst[3] = {phi, cs, cl};
-    const void* src[3] = {h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2]};
-    int rc = copy_fields(h, dst, src, where == PF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
-    if (rc) return rc;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    const size_t bytes = (size_t)h->P.cells() * h->P.elem();
+    void* out[3] = {phi, cs, cl};
+    const pf::Fields& st = h->buf[h->cur ^ 1];
+    void* tgt[3] = {phi, cs, cl};
+    if (where == PF_HOST) {
+        tgt[0] = st.phi; tgt[1] = st.c; tgt[2] = st.d;
+    }
+    cudaError_t e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
+    if (where == PF_HOST) {
+        for (int f = 0; f < 3; ++f) {
+            e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+        }
+    }
+    e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     return PF_OK;
 }
@@ -227,13 +247,15 @@ int pf_step(pf_handle* h, int64_t n) {
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
     const pf::HostProblem& P = h->P;
     for (int64_t s = 0; s < n; ++s) {
+        const pf::Fields& in = h->buf[h->cur];
+        const pf::Fields& out = h->buf[h->cur ^ 1];
         pf::StepLaunch a;
         a.prob = &P;
-        a.phi_in = h->buf[h->cur][0]; a.cs_in = h->buf[h->cur][1]; a.cl_in = h->buf[h->cur][2];
-        a.phi_out = h->buf[h->cur ^ 1][0]; a.cs_out = h->buf[h->cur ^ 1][1]; a.cl_out = h->buf[h->cur ^ 1][2];
+        a.phi_in = in.phi; a.c_in = in.c; a.d_in = in.d; a.clo_in = in.clo;
+        a.phi_out = out.phi; a.c_out = out.c; a.d_out = out.d; a.clo_out = out.clo;
         a.step = h->step;
         a.shifts = h->shifts;
-        a.zchunk = 0;
+        a.zchunk = h->zchunk;
         a.stream = h->stream;
         cudaError_t e = pf::launch_step(a);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
@@ -242,9 +264,7 @@ int pf_step(pf_handle* h, int64_t n) {
         if (P.shift) {
             const double t = (double)h->step * P.dt;
             while (P.v_pull * t >= (double)(h->shifts + 1) * P.dx) {
-                e = pf::launch_shift(P, h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2],
-                                     h->buf[h->cur ^ 1][0], h->buf[h->cur ^ 1][1],
-                                     h->buf[h->cur ^ 1][2], h->stream);
+                e = pf::launch_shift(P, h->buf[h->cur], h->buf[h->cur ^ 1], h->stream);
                 if (e != cudaSuccess) return cuda_fail(h, e, "shift kernel launch");
                 h->cur ^= 1;
                 h->shifts += 1;
@@ -262,10 +282,9 @@ static int fetch_results(pf_handle* h, int count) {
     return PF_OK;
 }
 
-static int energy_solute(pf_handle* h) {
-    cudaError_t e = pf::launch_energy_solute(h->P, h->buf[h->cur][0], h->buf[h->cur][1],
-                                             h->buf[h->cur][2], h->step, h->shifts, h->scratch,
-                                             h->dres, h->stream);
+static int energy_solute(pf_handle* h, bool with_energy) {
+    cudaError_t e = pf::launch_energy_solute(h->P, h->buf[h->cur], h->step, h->shifts, with_energy,
+                                             h->scratch, h->dres, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "energy kernel launch");
     return fetch_results(h, 2);
 }
@@ -273,7 +292,7 @@ static int energy_solute(pf_handle* h) {
 int pf_energy(pf_handle* h, double* F) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!F) return fail(h, PF_EINVAL, "null output");
-    int rc = energy_solute(h);
+    int rc = energy_solute(h, true);
     if (rc) return rc;
     *F = h->hres[0];
     if (!std::isfinite(*F)) return fail(h, PF_ENONFINITE, "non-finite free energy");
@@ -283,7 +302,7 @@ int pf_energy(pf_handle* h, double* F) {
 int pf_solute_total(pf_handle* h, double* S) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!S) return fail(h, PF_EINVAL, "null output");
-    int rc = energy_solute(h);
+    int rc = energy_solute(h, false);
     if (rc) return rc;
     *S = h->hres[1];
     if (!std::isfinite(*S)) return fail(h, PF_ENONFINITE, "non-finite solute total");
@@ -293,8 +312,7 @@ int pf_solute_total(pf_handle* h, double* S) {
 int pf_front(pf_handle* h, double* x_front, double* v_front, double* c_max) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!x_front || !v_front || !c_max) return fail(h, PF_EINVAL, "null output");
-    cudaError_t e = pf::launch_front(h->P, h->buf[h->cur][0], h->buf[h->cur][1], h->buf[h->cur][2],
-                                     h->scratch, h->dres, h->stream);
+    cudaError_t e = pf::launch_front(h->P, h->buf[h->cur], h->scratch, h->dres, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "front kernel launch");
     int rc = fetch_results(h, 2);
     if (rc) return rc;

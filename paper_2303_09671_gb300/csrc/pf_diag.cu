@@ -1,5 +1,6 @@
 // pf_diag.cu -- FP64 diagnostics (discrete free energy, total solute, front,
-// c_max), the 1D moving-window shift and a non-finite check.
+// c_max), the 1D moving-window shift and the conversions between the
+// caller's (phi, c_s, c_l) and the device state (phi, c, d).
 //
 // Reductions are deterministic: a fixed grid of DIAG_BLOCKS blocks writes one
 // partial per block (warp-shuffle tree inside the block), and a single block
@@ -62,25 +63,40 @@ __device__ void block_reduce2(double& a, double& b) {
     }
 }
 
+// state accessors: c (with its FP32 low word), d -> c_s, c_l in FP64
 template <typename T>
+struct StateView {
+    const T* phi;
+    const T* c;
+    const T* d;
+    const T* clo;   // nullptr in FP64
+    __device__ __forceinline__ double cval(long long i) const {
+        return (double)c[i] + (clo ? (double)clo[i] : 0.0);
+    }
+};
+
+template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(DIAG_THREADS)
-energy_solute_kernel(const T* __restrict__ phi, const T* __restrict__ cs,
-                     const T* __restrict__ cl, DiagConsts C, double* __restrict__ part) {
+energy_solute_kernel(StateView<T> S, DiagConsts C, double* __restrict__ part) {
     const long long N = (long long)C.n[0] * C.n[1] * C.n[2];
-    // Laplacian stencil weights (units of 1/dx^2), centre excluded
     double eF = 0.0, eS = 0.0;
     const double one_m_ke = 1.0 - C.k_e, log_ke = log(C.k_e);
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
+        const double cc = S.cval(c);
+        eS += cc;
+        if (!ENERGY) continue;
         const int i = (int)(c % C.n[0]);
         const int j = (int)((c / C.n[0]) % C.n[1]);
         const int k = (int)(c / ((long long)C.n[0] * C.n[1]));
-        const double f = (double)phi[c], s = (double)cs[c], l = (double)cl[c];
+        const double f = (double)S.phi[c], d = (double)S.d[c];
         const double p = p_d(C, f);
+        const double s = cc + (1.0 - p) * d, l = cc - p * d;
         const double theta = C.theta0 - C.G_theta * (((double)i + 0.5) * C.dx);
         const double fs = -one_m_ke * theta + s * (log(s) - log_ke - 1.0);
         const double fl = l * (log(l) - 1.0);
         const double fdw = f * f * (1.0 - f) * (1.0 - f);
+        // gradient energy: each stencil pair once, weights of the Laplacian
         double gs = 0.0;
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
@@ -94,11 +110,10 @@ energy_solute_kernel(const T* __restrict__ phi, const T* __restrict__ cs,
                     else if (C.lap == 7) w = (nzc == 1) ? 1.0 : 0.0;
                     else w = (nzc == 1) ? 1.0 / 3.0 : (nzc == 2 ? 1.0 / 6.0 : 0.0);
                     if (w == 0.0) continue;
-                    const double dphi = fetch_phi(C, phi, i + dx, j + dy, k + dz) - f;
+                    const double dphi = fetch_phi(C, S.phi, i + dx, j + dy, k + dz) - f;
                     gs += w * dphi * dphi;
                 }
         eF += C.H * fdw + p * fs + (1.0 - p) * fl + 0.5 * C.sigma * 0.5 * gs / (C.dx * C.dx);
-        eS += p * s + (1.0 - p) * l;
     }
     block_reduce2<false>(eF, eS);
     if (threadIdx.x == 0) {
@@ -123,13 +138,12 @@ finish_sum2(const double* __restrict__ part, int nb, double scale, double* __res
 
 template <typename T>
 __global__ void __launch_bounds__(DIAG_THREADS)
-front_kernel(const T* __restrict__ phi, const T* __restrict__ cs, const T* __restrict__ cl,
-             DiagConsts C, double* __restrict__ part) {
+front_kernel(StateView<T> S, DiagConsts C, double* __restrict__ part) {
     const long long rows = (long long)C.n[1] * C.n[2];
     double xf = -INFINITY, cm = -INFINITY;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
          r += (long long)gridDim.x * blockDim.x) {
-        const T* prow = phi + r * C.n[0];
+        const T* prow = S.phi + r * C.n[0];
         for (int i = C.n[0] - 2; i >= 0; --i) {
             const double a = (double)prow[i], b = (double)prow[i + 1];
             if (a >= 0.5 && b < 0.5) {
@@ -137,10 +151,7 @@ front_kernel(const T* __restrict__ phi, const T* __restrict__ cs, const T* __res
                 break;
             }
         }
-        for (int i = 0; i < C.n[0]; ++i) {
-            const double p = p_d(C, (double)prow[i]);
-            cm = fmax(cm, p * (double)cs[r * C.n[0] + i] + (1.0 - p) * (double)cl[r * C.n[0] + i]);
-        }
+        for (int i = 0; i < C.n[0]; ++i) cm = fmax(cm, S.cval(r * C.n[0] + i));
     }
     block_reduce2<true>(xf, cm);
     if (threadIdx.x == 0) {
@@ -163,28 +174,55 @@ finish_max2(const double* __restrict__ part, int nb, double* __restrict__ out) {
     }
 }
 
+// store an FP64 value of c as the state's c (and low word in FP32)
 template <typename T>
-__global__ void shift_kernel(const T* __restrict__ pi, const T* __restrict__ si,
-                             const T* __restrict__ li, T* __restrict__ po, T* __restrict__ so,
-                             T* __restrict__ lo, int n, T fp, T fs, T fl) {
+__device__ __forceinline__ void put_c(T* c, T* clo, long long i, double v) {
+    const T hi = (T)v;
+    c[i] = hi;
+    if (clo) clo[i] = (T)(v - (double)hi);
+}
+
+template <typename T>
+__global__ void shift_kernel(StateView<T> in, T* po, T* co, T* dout, T* clo_out, int n,
+                             double fphi, double fc, double fd) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (i < n - 1) {
-            po[i] = pi[i + 1]; so[i] = si[i + 1]; lo[i] = li[i + 1];
+            po[i] = in.phi[i + 1];
+            co[i] = in.c[i + 1];
+            dout[i] = in.d[i + 1];
+            if (clo_out) clo_out[i] = in.clo[i + 1];
         } else {
-            po[i] = fp; so[i] = fs; lo[i] = fl;
+            po[i] = (T)fphi;
+            dout[i] = (T)fd;
+            put_c(co, clo_out, i, fc);
         }
     }
 }
 
 template <typename T>
-__global__ void finite_kernel(const T* __restrict__ a, const T* __restrict__ b,
-                              const T* __restrict__ c, long long n, int* flag) {
-    int bad = 0;
+__global__ void to_state_kernel(const T* __restrict__ phi, const T* __restrict__ cs,
+                                const T* __restrict__ cl, long long n, DiagConsts C, T* po,
+                                T* co, T* dout, T* clo) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        bad |= !isfinite(a[i]) | !isfinite(b[i]) | !isfinite(c[i]);
-    bad = __syncthreads_or(bad);
-    if (bad && threadIdx.x == 0) atomicExch(flag, 1);
+         i += (long long)gridDim.x * blockDim.x) {
+        const double f = (double)phi[i], s = (double)cs[i], l = (double)cl[i];
+        const double p = p_d(C, f);
+        po[i] = phi[i];
+        put_c(co, clo, i, p * s + (1.0 - p) * l);
+        dout[i] = (T)(s - l);
+    }
+}
+
+template <typename T>
+__global__ void from_state_kernel(StateView<T> S, long long n, DiagConsts C, T* phi, T* cs, T* cl) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double f = (double)S.phi[i], c = S.cval(i), d = (double)S.d[i];
+        const double p = p_d(C, f);
+        phi[i] = S.phi[i];
+        cs[i] = (T)(c + (1.0 - p) * d);
+        cl[i] = (T)(c - p * d);
+    }
 }
 
 static DiagConsts make_diag(const HostProblem& P, int64_t step, int64_t shifts) {
@@ -210,58 +248,82 @@ static DiagConsts make_diag(const HostProblem& P, int64_t step, int64_t shifts) 
     return C;
 }
 
-cudaError_t launch_energy_solute(const HostProblem& P, const void* phi, const void* cs,
-                                 const void* cl, int64_t step, int64_t shifts,
-                                 double* scratch, double* out, cudaStream_t s) {
+template <typename T>
+static StateView<T> view(const Fields& f) {
+    return StateView<T>{(const T*)f.phi, (const T*)f.c, (const T*)f.d, (const T*)f.clo};
+}
+
+cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t step,
+                                 int64_t shifts, bool with_energy, double* scratch, double* out,
+                                 cudaStream_t s) {
     const DiagConsts C = make_diag(P, step, shifts);
-    if (P.precision == 1)
-        energy_solute_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
-            (const double*)phi, (const double*)cs, (const double*)cl, C, scratch);
-    else
-        energy_solute_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
-            (const float*)phi, (const float*)cs, (const float*)cl, C, scratch);
+    if (P.precision == 1) {
+        if (with_energy) energy_solute_kernel<double, true><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+        else energy_solute_kernel<double, false><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+    } else {
+        if (with_energy) energy_solute_kernel<float, true><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
+        else energy_solute_kernel<float, false><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
+    }
     finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, C.dV, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_front(const HostProblem& P, const void* phi, const void* cs,
-                         const void* cl, double* scratch, double* out, cudaStream_t s) {
+cudaError_t launch_front(const HostProblem& P, const Fields& f, double* scratch, double* out,
+                         cudaStream_t s) {
     const DiagConsts C = make_diag(P, 0, 0);
     if (P.precision == 1)
-        front_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
-            (const double*)phi, (const double*)cs, (const double*)cl, C, scratch);
+        front_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
     else
-        front_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
-            (const float*)phi, (const float*)cs, (const float*)cl, C, scratch);
+        front_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
     finish_max2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shift(const HostProblem& P, const void* pi, const void* si, const void* li,
-                         void* po, void* so, void* lo, cudaStream_t s) {
+static double p_host(const HostProblem& P, double f) {
+    const double g = f * (1.0 - f);
+    const double h = (P.interp == 1) ? f * f * (3.0 - 2.0 * f) : f * f * f * (6.0 * f * f - 15.0 * f + 10.0);
+    return h + P.a * (f - 0.5) * g * g;
+}
+
+cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& out, cudaStream_t s) {
     const int n = (int)P.n[0];
     const int blocks = (n + 255) / 256;
+    const double p = p_host(P, P.dir_phi);
+    const double fc = p * P.dir_cs + (1.0 - p) * P.dir_cl, fd = P.dir_cs - P.dir_cl;
     if (P.precision == 1)
-        shift_kernel<double><<<blocks, 256, 0, s>>>((const double*)pi, (const double*)si,
-                                                    (const double*)li, (double*)po, (double*)so,
-                                                    (double*)lo, n, P.dir_phi, P.dir_cs, P.dir_cl);
+        shift_kernel<double><<<blocks, 256, 0, s>>>(view<double>(in), (double*)out.phi, (double*)out.c,
+                                                    (double*)out.d, nullptr, n, P.dir_phi, fc, fd);
     else
-        shift_kernel<float><<<blocks, 256, 0, s>>>((const float*)pi, (const float*)si,
-                                                   (const float*)li, (float*)po, (float*)so,
-                                                   (float*)lo, n, (float)P.dir_phi,
-                                                   (float)P.dir_cs, (float)P.dir_cl);
+        shift_kernel<float><<<blocks, 256, 0, s>>>(view<float>(in), (float*)out.phi, (float*)out.c,
+                                                   (float*)out.d, (float*)out.clo, n, P.dir_phi, fc, fd);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finite_check(const HostProblem& P, const void* phi, const void* cs,
-                                const void* cl, int* flag, cudaStream_t s) {
+cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* cs, const void* cl,
+                            const Fields& out, cudaStream_t s) {
+    const DiagConsts C = make_diag(P, 0, 0);
     const long long n = P.cells();
     if (P.precision == 1)
-        finite_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
-            (const double*)phi, (const double*)cs, (const double*)cl, n, flag);
+        to_state_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const double*)phi, (const double*)cs, (const double*)cl, n, C, (double*)out.phi,
+            (double*)out.c, (double*)out.d, nullptr);
     else
-        finite_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
-            (const float*)phi, (const float*)cs, (const float*)cl, n, flag);
+        to_state_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const float*)phi, (const float*)cs, (const float*)cl, n, C, (float*)out.phi,
+            (float*)out.c, (float*)out.d, (float*)out.clo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
+                              cudaStream_t s) {
+    const DiagConsts C = make_diag(P, 0, 0);
+    const long long n = P.cells();
+    if (P.precision == 1)
+        from_state_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            view<double>(in), n, C, (double*)phi, (double*)cs, (double*)cl);
+    else
+        from_state_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            view<float>(in), n, C, (float*)phi, (float*)cs, (float*)cl);
     return cudaGetLastError();
 }
 

@@ -23,10 +23,16 @@ struct HostProblem {
     size_t elem() const { return precision == 1 ? sizeof(double) : sizeof(float); }
 };
 
+// Device state: phi, c = p c_s + (1-p) c_l, d = c_s - c_l and, in FP32, the
+// low word c_lo of c (NULL in FP64).
+struct Fields {
+    void *phi, *c, *d, *clo;
+};
+
 struct StepLaunch {
     const HostProblem* prob;
-    const void *phi_in, *cs_in, *cl_in;
-    void *phi_out, *cs_out, *cl_out;
+    const void *phi_in, *c_in, *d_in, *clo_in;
+    void *phi_out, *c_out, *d_out, *clo_out;
     int64_t step, shifts;   // clock of the input state
     int zchunk;             // planes per CTA along z (3D); <= 0: whole column
     cudaStream_t stream;
@@ -41,17 +47,17 @@ size_t step_smem_bytes(int precision, int dim);
 //   front:         out[0] = x_front (local, without the window offset; NaN if
 //                  none), out[1] = c_max
 size_t diag_scratch_doubles(const HostProblem& P);
-cudaError_t launch_energy_solute(const HostProblem& P, const void* phi, const void* cs,
-                                 const void* cl, int64_t step, int64_t shifts,
-                                 double* scratch, double* out, cudaStream_t s);
-cudaError_t launch_front(const HostProblem& P, const void* phi, const void* cs,
-                         const void* cl, double* scratch, double* out, cudaStream_t s);
-// moving window: out[i] = in[i+1] (i < n-1), out[n-1] = fresh value (1D)
-cudaError_t launch_shift(const HostProblem& P, const void* phi_in, const void* cs_in,
-                         const void* cl_in, void* phi_out, void* cs_out, void* cl_out,
+cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t step,
+                                 int64_t shifts, bool with_energy, double* scratch, double* out,
+                                 cudaStream_t s);
+cudaError_t launch_front(const HostProblem& P, const Fields& f, double* scratch, double* out,
                          cudaStream_t s);
-// non-finite check: *flag (device int) set to 1 if any value is not finite
-cudaError_t launch_finite_check(const HostProblem& P, const void* phi, const void* cs,
-                                const void* cl, int* flag, cudaStream_t s);
+// moving window: out[i] = in[i+1] (i < n-1), out[n-1] = the Dirichlet state (1D)
+cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& out, cudaStream_t s);
+// (phi, c_s, c_l) of the caller's precision <-> the device state (phi, c, d[, c_lo])
+cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* cs, const void* cl,
+                            const Fields& out, cudaStream_t s);
+cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
+                              cudaStream_t s);
 
 }  // namespace pf

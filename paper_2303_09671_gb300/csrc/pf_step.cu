@@ -10,12 +10,17 @@
 //   C  the face fluxes of plane k (x and y faces in shared memory, the z face
 //      to plane k+1 in registers): brackets of Eqs. cs_nonvar / cl_nonvar,
 //      combined into F_c = p_f F_s + (1-p_f) F_l and F_d = F_s - F_l
-//   D  conservative update of c and d, Euler update of phi, reconstruction of
-//      c_s, c_l with p(phi^{n+1}) (Sec. "Numerical technique")
+//   D  conservative update of c and d, Euler update of phi (Sec. "Numerical
+//      technique").  The state is held as (phi, c, d) with c = p c_s + (1-p) c_l
+//      (Eq. model1) and d = c_s - c_l; c_s = c + (1-p) d and c_l = c - p d are
+//      rebuilt from it when a plane is loaded.  In FP32, c carries a second
+//      FP32 word (compensated sum) so that its conservative update loses no
+//      solute to rounding.
 // 2D and 1D grids use the same kernel with one plane (and one row).
 #include <cstdint>
 #include <cstdio>
 #include <cmath>
+#include <algorithm>
 #include "pf_internal.cuh"
 #include "pf_kernels.h"
 
@@ -67,22 +72,26 @@ __device__ __forceinline__ void face_flux(const Consts<T>& C, int axis,
     const T q = Ms * Ml * (C.b * p + T(1) - p) * iMbar;
     const T ws = Ms * (T(1) - p) * iMbar;
     const T wl = bMlp * iMbar;
-    // gradient vectors of phi, Y, mu_s, mu_l at the face
-    T g2 = nrm[0] * nrm[0];
-    T dY = nrm[0] * nrm[1], ds = nrm[0] * nrm[2], dl = nrm[0] * nrm[3];
+    // gradient vectors of phi, Y, mu_s, mu_l at the face: normal component
+    // nrm[.], transverse components trn[.][e]
+    T gt2 = T(0), dYt = T(0), dst = T(0), dlt = T(0);
 #pragma unroll
     for (int e = 0; e < DIM - 1; ++e) {
-        g2 += trn[0][e] * trn[0][e];
-        dY += trn[0][e] * trn[1][e];
-        ds += trn[0][e] * trn[2][e];
-        dl += trn[0][e] * trn[3][e];
+        gt2 += trn[0][e] * trn[0][e];
+        dYt += trn[0][e] * trn[1][e];
+        dst += trn[0][e] * trn[2][e];
+        dlt += trn[0][e] * trn[3][e];
     }
-    const T r = T(1) / (g2 + C.delta2);
     const T ga = nrm[0];
+    const T gt2d = gt2 + C.delta2;
+    const T r = T(1) / (ga * ga + gt2d);
+    const T dY = ga * nrm[1] + dYt;
     const T normal = q * ga * dY * r;
     const T at = C.one_m_A * d * pdot * ga * r;
-    const T Fs = normal + Ms * (nrm[2] - ga * ds * r) + at * ws;
-    const T Fl = normal + Ml * (nrm[3] - ga * dl * r) - at * wl;
+    // tangential part d_a mu - g_a (g.grad mu) r, rewritten without cancellation
+    // as [d_a mu (|g_t|^2 + delta^2) - g_a (g_t.grad_t mu)] r
+    const T Fs = normal + Ms * (nrm[2] * gt2d - ga * dst) * r + at * ws;
+    const T Fl = normal + Ml * (nrm[3] * gt2d - ga * dlt) * r - at * wl;
     Fc = p * Fs + (T(1) - p) * Fl;
     Fd = Fs - Fl;
     (void)axis;
@@ -90,10 +99,10 @@ __device__ __forceinline__ void face_flux(const Consts<T>& C, int axis,
 
 template <typename T, int DIM, int TX, int TY>
 __global__ void __launch_bounds__(TX *(DIM >= 2 ? TY : 1))
-step_kernel(const T* __restrict__ phi_in, const T* __restrict__ cs_in,
-            const T* __restrict__ cl_in, T* __restrict__ phi_out,
-            T* __restrict__ cs_out, T* __restrict__ cl_out, Consts<T> C,
-            Clock<T> K, int zchunk) {
+step_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in,
+            const T* __restrict__ d_in, const T* __restrict__ clo_in,
+            T* __restrict__ phi_out, T* __restrict__ c_out, T* __restrict__ d_out,
+            T* __restrict__ clo_out, Consts<T> C, Clock<T> K, int zchunk) {
     using L = Tile<T, DIM, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -137,14 +146,18 @@ step_kernel(const T* __restrict__ phi_in, const T* __restrict__ cs_in,
                 my = map_coord(y0 - 2 + hy, ny, C.bc_lo[1], C.bc_hi[1]);
                 dir = dir || (my < 0);
             }
-            T f, cs, cl;
+            T f, cs, cl, p;
             if (dir) {
                 f = C.dir_phi; cs = C.dir_cs; cl = C.dir_cl;
+                p = p_of(C, f);
             } else {
                 const long long gi = (long long)mz * sz + (long long)my * sy + mx;
-                f = phi_in[gi]; cs = cs_in[gi]; cl = cl_in[gi];
+                f = phi_in[gi];
+                const T c = c_in[gi], d = d_in[gi];
+                p = p_of(C, f);
+                cs = c + (T(1) - p) * d;   // c_s, c_l from c = p c_s + (1-p) c_l, d = c_s - c_l
+                cl = c - p * d;
             }
-            const T p = p_of(C, f);
             const T mus = flog(cs) - C.log_ke;
             const T mul = flog(cl);
             RAW(0, s, h) = f;
@@ -348,16 +361,26 @@ step_kernel(const T* __restrict__ phi_in, const T* __restrict__ cs_in,
             dc += FzcU - FzcD;
             dd += FzdU - FzdD;
         }
-        const T f = RAW(0, s0, h), cs = RAW(1, s0, h), cl = RAW(2, s0, h);
-        const T p = p_of(C, f);
-        const T c = p * cs + (T(1) - p) * cl + C.dt * dc * C.inv_dx;
-        const T d = (cs - cl) + C.dt * dd * C.inv_dx;
-        const T fn = f + C.dt * PD(g0, r);
-        const T pn = p_of(C, fn);
         const long long gi = (long long)z * sz + (long long)gy * sy + gx;
-        phi_out[gi] = fn;
-        cs_out[gi] = c + (T(1) - pn) * d;
-        cl_out[gi] = c - pn * d;
+        const T f = RAW(0, s0, h);
+        const T dcv = C.dt * dc * C.inv_dx;
+        phi_out[gi] = f + C.dt * PD(g0, r);
+        d_out[gi] = d_in[gi] + C.dt * dd * C.inv_dx;
+        const T c = c_in[gi];
+        if (clo_in != nullptr) {
+            // c held as an unevaluated sum hi + lo of two FP32 numbers; the
+            // increment is added with an error-free transformation (Knuth's
+            // TwoSum) so that total solute is conserved to ~FP64 accuracy
+            const T s = c + dcv;
+            const T bv = s - c;
+            const T err = (c - (s - bv)) + (dcv - bv);
+            const T lo = clo_in[gi] + err;
+            const T hi = s + lo;
+            c_out[gi] = hi;
+            clo_out[gi] = lo - (hi - s);
+        } else {
+            c_out[gi] = c + dcv;
+        }
     };
 
     if constexpr (DIM < 3) {
@@ -406,23 +429,39 @@ static cudaError_t launch_tile(const StepLaunch& a, const Consts<T>& C, const Cl
     using L = Tile<T, DIM, TX, TY>;
     auto kern = step_kernel<T, DIM, TX, TY>;
     static bool configured = false;
+    static int per_sm = 1, sms = 1;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)L::BYTES);
         if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * L::TYe, L::BYTES);
+        if (per_sm < 1) per_sm = 1;
         configured = true;
     }
     dim3 block(TX * L::TYe);
     dim3 grid((C.n[0] + TX - 1) / TX, (DIM >= 2) ? (C.n[1] + TY - 1) / TY : 1, 1);
     int zchunk = 1;
     if (DIM == 3) {
-        zchunk = a.zchunk > 0 ? a.zchunk : C.n[2];
+        if (a.zchunk > 0) {
+            zchunk = a.zchunk;
+        } else {
+            // split the z-march so that there are at least four CTAs per
+            // resident slot; each chunk re-reads a 2-plane halo in z
+            const long long tiles = (long long)grid.x * grid.y;
+            const long long want = 4LL * per_sm * sms;
+            const int chunks = (int)std::max(1LL, (want + tiles - 1) / tiles);
+            zchunk = std::max(8, (C.n[2] + chunks - 1) / chunks);
+        }
         grid.z = (C.n[2] + zchunk - 1) / zchunk;
     }
     kern<<<grid, block, L::BYTES, a.stream>>>(
-        static_cast<const T*>(a.phi_in), static_cast<const T*>(a.cs_in),
-        static_cast<const T*>(a.cl_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.cs_out),
-        static_cast<T*>(a.cl_out), C, K, zchunk);
+        static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in),
+        static_cast<const T*>(a.d_in), static_cast<const T*>(a.clo_in),
+        static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out), static_cast<T*>(a.d_out),
+        static_cast<T*>(a.clo_out), C, K, zchunk);
     return cudaGetLastError();
 }
 

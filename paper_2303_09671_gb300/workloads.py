@@ -68,7 +68,7 @@ def stable_dt(pr: dict) -> float:
 
 def scaled_params(dim, n, dx, k_e, theta, D_s, *, A=0.4, b=None, a=0.0, eps=1.0,
                   alpha=1.0, lap=None, bc_lo=None, bc_hi=None, interp="quintic",
-                  mobility="Dc", delta=1e-4, G_theta=0.0, v_pull=0.0, x0=0.0,
+                  mobility="Dc", delta=1e-3, G_theta=0.0, v_pull=0.0, x0=0.0,
                   c_inf=1.0, shift=False, dt_factor=0.9, dt=None, form="cd"):
     """Parameter dict in scaled units (keys shared by the oracle and the library)."""
     H = theta * (1.0 - k_e) ** 2 / (I_DW * eps)
@@ -215,8 +215,10 @@ def random_state(dim, n, dx=0.5, k_e=0.1, theta=2.0, D_s=0.1, seed=0, amp=0.3, w
     else:
         mod = np.zeros((1,))
     phi = tanh_profile(x, front + wiggle * dx * mod)
+    # c_l varies by k_e*amp only: the normal fluxes change c_s and c_l by the
+    # same amount, so c_l variations must stay below c_s ~ k_e c_l
     cs = k_e * pr["c_inf"] * (1.0 + amp * _smooth_field(rng, shape, dx))
-    cl = pr["c_inf"] * (1.0 + amp * _smooth_field(rng, shape, dx))
+    cl = pr["c_inf"] * (1.0 + k_e * amp * _smooth_field(rng, shape, dx))
     return pr, phi, cs, cl
 
 
