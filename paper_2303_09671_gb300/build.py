@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # --prec-div=false: FP32 divisions use the approximate reciprocal (FP64 is unaffected)
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-           "--prec-div=false", "-Xptxas", "-warn-spills"]
+           "-Xptxas", "-warn-spills"]
 
 
 def nvcc() -> str:

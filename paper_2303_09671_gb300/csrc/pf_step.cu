@@ -54,6 +54,9 @@ struct Tile {
 // the two cells' centred differences; phi, c_s, c_l, d and phidot at the face
 // are the means of the two cells; p, Mbar, q_n and the weights are evaluated
 // at the face phi.
+template <typename T, int TX, int TY, int MINB>
+cudaError_t launch_step3d_tile(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K);
+
 template <typename T, int DIM>
 __device__ __forceinline__ void face_flux(const Consts<T>& C, int axis,
                                           T phiL, T phiR, T csL, T csR, T clL, T clR,
@@ -507,7 +510,9 @@ static cudaError_t launch_T(const StepLaunch& a) {
     const Clock<T> K = make_clock<T>(P, a.step, a.shifts);
     if (P.dim == 1) return launch_tile<T, 1, 128, 1>(a, C, K);
     if (P.dim == 2) return launch_tile<T, 2, 32, 8>(a, C, K);
-    return launch_tile<T, 3, 32, 8>(a, C, K);
+    if (a.use_generic3d) return launch_tile<T, 3, 32, 8>(a, C, K);
+    if constexpr (sizeof(T) == 4) return launch_step3d_tile<T, 32, 8, 4>(a, C, K);
+    else return launch_step3d_tile<T, 32, 8, 2>(a, C, K);
 }
 
 cudaError_t launch_step(const StepLaunch& a) {
