@@ -163,6 +163,70 @@ def run_reference(args):
     return 0
 
 
+def kv_sweep_inputs(n_inst=256, seed=4):
+    """256 1D pulled fronts: lengths uniform in 512..8192 cells (seeded), pulling
+    velocities log-spaced in 1e-3..10 (scaled), frozen gradient 5.25e-3 per W."""
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(512, 8193, size=n_inst)
+    vs = np.logspace(-3, 1, n_inst)
+    prs, phis, css, cls = [], [], [], []
+    for n, v in zip(lengths, vs):
+        pr, phi, cs, cl = wl.pulled_front_1d(N=int(n), dx=0.5, V=float(v), G_theta=5.25e-3,
+                                             front_cell=int(n) // 4, A=1.0, b=1.0)
+        prs.append(pr)
+        phis.append(phi)
+        css.append(cs)
+        cls.append(cl)
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    return lengths, vs, prs, dts, np.concatenate(phis), np.concatenate(css), np.concatenate(cls)
+
+
+def run_kv_sweep(args):
+    """Batched k(V) sweep (one persistent launch per chunk, CUDA graph) against a
+    per-instance loop of the single-handle path, same steps, same GPU."""
+    import torch
+    from paper_2303_09671_gb300 import pf
+    lengths, vs, prs, dts, phi, cs, cl = kv_sweep_inputs()
+    K = args.steps
+    f32 = [a.astype(np.float32) for a in (phi, cs, cl)]
+    spl = max(1, K // 4)
+    pf.run_batch(prs[0], lengths, vs, *f32, dt=dts, max_steps=spl, steps_per_launch=spl,
+                 launches_per_graph=1, tol=-1.0)                     # warm-up (autotune, module load)
+    t0 = time.perf_counter()
+    res = pf.run_batch(prs[0], lengths, vs, *f32, dt=dts, max_steps=K, steps_per_launch=spl,
+                       launches_per_graph=4, tol=-1.0)
+    batch_wall = time.perf_counter() - t0
+    batch_s = res["gpu_ms"] * 1e-3
+    # per-instance loop of the single-handle kernel
+    stream = torch.cuda.Stream()
+    loop_s, o = 0.0, 0
+    with torch.cuda.stream(stream):
+        for pr, n, dt in zip(prs, lengths, dts):
+            n = int(n)
+            with pf.Sim(dict(pr, dt=dt), "fp32", stream=stream.cuda_stream) as s:
+                s.set_fields(f32[0][o:o + n], f32[1][o:o + n], f32[2][o:o + n])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(K)
+                e1.record(stream)
+                e1.synchronize()
+                loop_s += e0.elapsed_time(e1) * 1e-3
+            o += n
+    cells = int(np.sum(lengths))
+    out = {"metric": "1D pulled-front instance-steps/s (256 instances, 512..8192 cells)",
+           "value": len(lengths) * K / batch_s, "unit": "instance-steps/s", "n_gpus": 1, "steps": K,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "kv-sweep: 256 1D pulled fronts, lengths U{512..8192} (seed 4), "
+                                  "V log-spaced 1e-3..10, G=5.25e-3, A=1, b=1, fixed step budget",
+                      "cells_total": cells, "cells_per_thread": res["cells_per_thread"]},
+           "batch_gpu_s": batch_s, "batch_wall_s": batch_wall, "batch_launches": res["launches"],
+           "loop_gpu_s": loop_s, "loop_launches": len(lengths) * K,
+           "speedup_vs_loop": loop_s / batch_s,
+           "cell_updates_per_s": cells * K / batch_s}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,8 +236,11 @@ def main():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "kv-sweep"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "kv-sweep":
+        return run_kv_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
 

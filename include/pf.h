@@ -160,6 +160,59 @@ int pf_set_clock(pf_handle* h, int64_t step, int64_t shifts);
  * over p in [0,1] at c_s = k_e c_inf, c_l = c_inf. */
 int pf_stable_dt(const pf_grid* grid, const pf_params* params, double* dt);
 
+/* ------------------------------------------------------------------------
+ * Batched 1D pulled fronts: the k(V) sweep of Sec. "Effect of parameter A on
+ * velocity-dependent partition coefficient" (k_v = c_inf / c_max at steady
+ * state) for many instances of different lengths and pulling velocities in one
+ * persistent launch per chunk of steps, replayed as a CUDA graph.
+ *
+ * Every instance is a 1D directional-solidification problem: frozen
+ * temperature theta(x,t) = theta_ref - G_theta ((x - x0) - v t) (Eq. ds1), no-flux
+ * cold end, fixed hot end (bc.dir_*), moving window (Sec. "Numerical
+ * technique"), and the shared model parameters of `params` (params.v_pull,
+ * params.dt and params.shift are ignored; precision FP32 or FP64).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int n_instances;
+    const int64_t* n;      /* cells per instance, 8..8192 (FP32) or 8..4096 (FP64) */
+    const double* v_pull;  /* pulling velocity per instance, >= 0 */
+    const double* dt;      /* time step per instance; NULL or <= 0: 0.9 pf_stable_dt
+                              capped at 0.5 dx / v */
+    const void* phi0;      /* initial fields, instances packed one after another,  */
+    const void* cs0;       /* host memory, element type of params.precision        */
+    const void* cl0;
+    double dx;
+    pf_bc bc;              /* lo[0] must be PF_BC_NOFLUX, hi[0] PF_BC_DIRICHLET */
+    pf_params params;
+    int64_t max_steps;         /* per instance */
+    int64_t steps_per_launch;  /* steps of one persistent launch (> 0) */
+    int launches_per_graph;    /* launches captured in one CUDA graph (> 0) */
+    int64_t check_every;       /* steps between k_v evaluations (> 0) */
+    double window;             /* minimum time between the two k_v samples of a rate */
+    double tol;                /* converged when |dk_v/dt| < tol */
+    int cells_per_thread;      /* 1, 2, 4 or 8; 0 = autotune */
+} pf_batch_desc;
+
+typedef struct {
+    double* k_v;           /* per instance: last k_v = c_inf / c_max */
+    double* dkdt;          /* per instance: last |dk_v/dt| */
+    double* t;             /* per instance: simulated time reached */
+    int64_t* steps;        /* per instance: steps taken */
+    int* converged;        /* per instance: 1 if converged */
+    void* phi;             /* optional (may be NULL): packed final fields, host */
+    void* cs;
+    void* cl;
+    int cells_per_thread;  /* the value used (autotuned or given) */
+    int64_t launches;      /* batch-kernel launches issued */
+    double gpu_ms;         /* device time of the stepping (CUDA events) */
+} pf_batch_result;
+
+/* Run the batch until every instance has converged or taken max_steps
+ * steps.  All arrays are caller-owned host memory of n_instances entries (the
+ * optional field arrays hold the sum of n).  Allocates and frees its own device
+ * memory; synchronises `stream`.  Returns PF_EINVAL for invalid descriptors. */
+int pf_run_batch(const pf_batch_desc* desc, pf_batch_result* res, void* stream);
+
 /* Message describing the last error on h (or the last pf_create failure when
  * h is NULL).  Owned by the library; valid until the next call on h. */
 const char* pf_last_error(pf_handle* h);

@@ -6,7 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include "../../include/pf.h"
+#include "pf.h"
 #include "pf_kernels.h"
 
 struct pf_handle {
@@ -105,6 +105,11 @@ std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
 }
 
 }  // namespace
+
+namespace pf {
+// message returned by pf_last_error(NULL) (failed pf_create / pf_run_batch)
+void set_create_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace pf
 
 extern "C" {
 

@@ -1,0 +1,708 @@
+// pf_batch.cu -- batched 1D pulled fronts in one persistent launch.
+//
+// Each CTA owns one 1D directional-solidification instance (frozen
+// temperature of Eq. ds1, moving window of Sec. "Numerical technique",
+// no-flux cold end, fixed hot end) and keeps its whole state in shared memory
+// for `nsteps` steps: phi, c = p c_s + (1-p) c_l, d = c_s - c_l, the diffusion
+// potentials and the phase-field rate.  Global memory is touched only at the
+// start and the end of a launch.  The discrete step is the one of the other
+// kernels (Eq. phasefield_nonvar with the re-derived driving force at cells;
+// the brackets of Eqs. cs_nonvar / cl_nonvar at faces; forward Euler on phi, c,
+// d).  Every `check_every` steps the CTA evaluates k_v = c_inf / c_max (Sec.
+// "Effect of parameter A on velocity-dependent partition coefficient") and
+// marks the instance converged once |dk_v/dt| stays below a tolerance over a
+// window of at least `window` time units; converged instances return at once in
+// later launches.  Instances are grouped by the block size an autotuner picks
+// for their length; the groups run concurrently on forked streams and the whole
+// chunk of launches is captured in a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+#include "pf.h"
+#include "pf_internal.cuh"
+#include "pf_kernels.h"
+
+namespace pf {
+
+constexpr int BATCH_J = 8;   // cells per thread at most
+
+// per-instance persistent state (device)
+struct BatchState {
+    long long off;      // offset of the instance's cells in the packed field arrays
+    int n;              // cells
+    int converged;
+    long long step, shifts;
+    double k_prev, t_prev, k_last, dkdt_last;
+};
+
+template <typename T>
+struct BatchArgs {
+    T* phi;             // packed fields
+    T* c;
+    T* d;
+    BatchState* st;
+    const int* ids;     // instances of this launch group
+    const double* v;    // per-instance pulling velocity
+    const double* dt;   // per-instance time step
+    int count;
+    int nsteps;
+    int check_every;
+    double tol, window;
+    Consts<T> C;        // shared model parameters (dt unused; per instance)
+    double theta_ref, G_theta, x0, c_inf;
+    T gphi, gcs, gcl, gmus, gmul;   // Dirichlet (hot end) ghost
+    T fc, fd;                       // fresh-layer state of the moving window
+};
+
+template <typename T>
+__device__ __forceinline__ T frcp_b(T x) { return T(1) / x; }
+
+// 1D face (L, R): normal differences only
+template <typename T>
+__device__ __forceinline__ void face1(const Consts<T>& C, T fL, T fR, T csL, T csR, T clL, T clR,
+                                      T pdL, T pdR, T nphi, T nY, T nS, T nL, T& Fc, T& Fd) {
+    const T f = T(0.5) * (fL + fR);
+    const T cs = T(0.5) * (csL + csR), cl = T(0.5) * (clL + clR);
+    const T d = cs - cl;
+    const T pdot = T(0.5) * (pdL + pdR);
+    const T p = p_of(C, f);
+    const T omp = T(1) - p;
+    const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
+    const T bMl = C.b * Ml;
+    const T iMbar = frcp_b(Ms * omp + bMl * p);
+    const T gt2d = C.delta2;
+    const T r = frcp_b(nphi * nphi + gt2d);
+    const T Ts = Ms * nS * gt2d;
+    const T Tl = Ml * nL * gt2d;
+    const T at = C.one_m_A * d * pdot * nphi;
+    const T q = Ms * Ml * (C.b * p + omp) * iMbar;
+    const T afn = (Ms - bMl) * p * omp * iMbar;
+    Fc = r * (q * nphi * nphi * nY + p * Ts + omp * Tl + at * afn);
+    Fd = r * (Ts - Tl + at);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
+batch_kernel(BatchArgs<T> a) {
+    const int inst = a.ids[blockIdx.x];
+    BatchState& S = a.st[inst];
+    if (S.converged) return;
+    const int n = S.n;
+    const Consts<T>& C = a.C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sPhi = reinterpret_cast<T*>(smem);          // n
+    T* sC = sPhi + n;                               // n
+    T* sD = sC + n;                                 // n
+    T* sMs = sD + n;                                // n: mu_s
+    T* sMl = sMs + n;                               // n: mu_l
+    T* sPd = sMl + n;                               // n: phase-field rate
+    __shared__ double red[NT / 32];
+    __shared__ int s_done;
+
+    const int tid = threadIdx.x;
+    const long long off = S.off;
+    for (int i = tid; i < n; i += NT) {
+        sPhi[i] = a.phi[off + i];
+        sC[i] = a.c[off + i];
+        sD[i] = a.d[off + i];
+    }
+    long long step = S.step, shifts = S.shifts;
+    double k_prev = S.k_prev, t_prev = S.t_prev, k_last = S.k_last, dkdt_last = S.dkdt_last;
+    int converged = 0;
+    const double v = a.v[inst];
+    const T dt = T(a.dt[inst]);
+    const T dtdx = dt * C.inv_dx;
+    if (tid == 0) s_done = 0;
+    __syncthreads();
+
+    auto cs_cl = [&](int i, T& p, T& cs, T& cl) {
+        p = p_of(C, sPhi[i]);
+        cs = sC[i] + (T(1) - p) * sD[i];
+        cl = sC[i] - p * sD[i];
+    };
+
+    for (int it = 0; it < a.nsteps; ++it) {
+        const double t = (double)step * a.dt[inst];
+        const T theta0 = T(a.theta_ref + a.G_theta * (a.x0 + v * t - (double)shifts * (double)C.dx));
+        // P1: diffusion potentials
+        for (int i = tid; i < n; i += NT) {
+            T p, cs, cl;
+            cs_cl(i, p, cs, cl);
+            sMs[i] = flog(cs) - C.log_ke;
+            sMl[i] = flog(cl);
+        }
+        __syncthreads();
+        // P2: phase-field rate (cold end: mirror ghost; hot end: Dirichlet ghost)
+        for (int i = tid; i < n; i += NT) {
+            const int im = (i == 0) ? 0 : i - 1;
+            const T fc = sPhi[i];
+            const T fW = sPhi[im];
+            const T fE = (i == n - 1) ? a.gphi : sPhi[i + 1];
+            const T mW_s = sMs[im], mW_l = sMl[im];
+            const T mE_s = (i == n - 1) ? a.gmus : sMs[i + 1];
+            const T mE_l = (i == n - 1) ? a.gmul : sMl[i + 1];
+            T p, cs, cl;
+            cs_cl(i, p, cs, cl);
+            const T mus = sMs[i], mul = sMl[i];
+            const T dp = dp_of(C, fc);
+            const T lap = (fW - T(2) * fc + fE) * C.inv_dx2;
+            const T gp = (fE - fW) * C.inv_2dx;
+            const T gs = (mE_s - mW_s) * C.inv_2dx;
+            const T gl = (mE_l - mW_l) * C.inv_2dx;
+            const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
+            const T bMl = C.b * Ml;
+            const T Msq = Ms * (T(1) - p);
+            const T iMbar = frcp_b(Msq + bMl * p);
+            const T d = cs - cl;
+            const T rr = frcp_b(gp * gp + C.delta2);
+            const T pq = p * (T(1) - p);
+            const T Kc = C.inv_Mphi + C.one_m_A * C.one_m_A * d * d * C.b * pq * rr * iMbar /
+                                          (C.b * p + T(1) - p);
+            const T theta = theta0 - C.G_theta * ((T(i) + T(0.5)) * C.dx);
+            const T dmu = mus - mul;
+            const T Dd = (Msq * (T(1) - C.A * (T(1) - p)) + C.A * bMl * p * p) * iMbar;
+            const T dG = cs * dmu - d - C.one_m_ke * theta - Dd * d * dmu;
+            const T dfdw = T(2) * fc * (T(1) - fc) * (T(1) - T(2) * fc);
+            const T R = C.sigma * lap - C.H * dfdw - dG * dp +
+                        C.one_m_A * d * pq * iMbar * (Ms * gs - bMl * gl) * gp * rr;
+            sPd[i] = R / Kc;
+        }
+        __syncthreads();
+        // P3: faces of each owned cell and the new state (kept in registers)
+        T nphi[BATCH_J], nc[BATCH_J], nd[BATCH_J];
+#pragma unroll
+        for (int j = 0; j < BATCH_J; ++j) {
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            T pL, csL, clL, pR, csR, clR, p0, cs0, cl0;
+            cs_cl(i, p0, cs0, cl0);
+            const T f0 = sPhi[i], ms0 = sMs[i], ml0 = sMl[i], pd0 = sPd[i];
+            const T Y0 = ml0 + p0 * (ms0 - ml0);
+            T FcL = T(0), FdL = T(0), FcR, FdR;
+            if (i > 0) {   // face (i-1, i); the face at the cold end is no-flux
+                cs_cl(i - 1, pL, csL, clL);
+                const T fL = sPhi[i - 1], msL = sMs[i - 1], mlL = sMl[i - 1];
+                const T YL = mlL + pL * (msL - mlL);
+                face1(C, fL, f0, csL, cs0, clL, cl0, sPd[i - 1], pd0, (f0 - fL) * C.inv_dx,
+                      (Y0 - YL) * C.inv_dx, (ms0 - msL) * C.inv_dx, (ml0 - mlL) * C.inv_dx, FcL, FdL);
+            }
+            if (i < n - 1) {
+                cs_cl(i + 1, pR, csR, clR);
+                const T fR = sPhi[i + 1], msR = sMs[i + 1], mlR = sMl[i + 1];
+                const T YR = mlR + pR * (msR - mlR);
+                face1(C, f0, fR, cs0, csR, cl0, clR, pd0, sPd[i + 1], (fR - f0) * C.inv_dx,
+                      (YR - Y0) * C.inv_dx, (msR - ms0) * C.inv_dx, (mlR - ml0) * C.inv_dx, FcR, FdR);
+            } else {       // face to the fixed hot-end ghost (phase-field rate 0)
+                const T gp = p_of(C, a.gphi);
+                const T YR = a.gmul + gp * (a.gmus - a.gmul);
+                face1(C, f0, a.gphi, cs0, a.gcs, cl0, a.gcl, pd0, T(0), (a.gphi - f0) * C.inv_dx,
+                      (YR - Y0) * C.inv_dx, (a.gmus - ms0) * C.inv_dx, (a.gmul - ml0) * C.inv_dx, FcR, FdR);
+            }
+            nphi[j] = f0 + dt * pd0;
+            nc[j] = sC[i] + dtdx * (FcR - FcL);
+            nd[j] = sD[i] + dtdx * (FdR - FdL);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < BATCH_J; ++j) {
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            sPhi[i] = nphi[j];
+            sC[i] = nc[j];
+            sD[i] = nd[j];
+        }
+        step += 1;
+        // moving window: drop the cold-end cell, append the fresh hot-end state
+        const double tn = (double)step * a.dt[inst];
+        while (v * tn >= (double)(shifts + 1) * (double)C.dx) {
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < BATCH_J; ++j) {
+                const int i = tid + j * NT;
+                if (i >= n) break;
+                if (i < n - 1) {
+                    nphi[j] = sPhi[i + 1]; nc[j] = sC[i + 1]; nd[j] = sD[i + 1];
+                } else {
+                    nphi[j] = a.gphi; nc[j] = a.fc; nd[j] = a.fd;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < BATCH_J; ++j) {
+                const int i = tid + j * NT;
+                if (i >= n) break;
+                sPhi[i] = nphi[j]; sC[i] = nc[j]; sD[i] = nd[j];
+            }
+            shifts += 1;
+        }
+        __syncthreads();
+        // steady-state check on k_v = c_inf / c_max
+        if (a.check_every > 0 && (step % a.check_every) == 0) {
+            double cm = -1e300;
+            for (int i = tid; i < n; i += NT) cm = fmax(cm, (double)sC[i]);
+            for (int o = 16; o > 0; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+            if ((tid & 31) == 0) red[tid >> 5] = cm;
+            __syncthreads();
+            if (tid == 0) {
+                double m = red[0];
+                for (int w = 1; w < NT / 32; ++w) m = fmax(m, red[w]);
+                const double k = a.c_inf / m;
+                k_last = k;
+                if (tn - t_prev >= a.window) {
+                    dkdt_last = fabs(k - k_prev) / (tn - t_prev);
+                    s_done = (t_prev > 0.0 && dkdt_last < a.tol) ? 1 : 0;
+                    k_prev = k;
+                    t_prev = tn;
+                }
+            }
+            __syncthreads();
+            if (s_done) {
+                converged = 1;
+                break;
+            }
+        }
+    }
+    for (int i = tid; i < n; i += NT) {
+        a.phi[off + i] = sPhi[i];
+        a.c[off + i] = sC[i];
+        a.d[off + i] = sD[i];
+    }
+    if (tid == 0) {
+        S.step = step;
+        S.shifts = shifts;
+        S.k_prev = k_prev;
+        S.t_prev = t_prev;
+        S.k_last = k_last;
+        S.dkdt_last = dkdt_last;
+        S.converged = converged;
+    }
+}
+
+
+// (phi, c_s, c_l) -> (phi, c, d) for packed instances
+template <typename T>
+__global__ void batch_to_state(const T* __restrict__ cs, const T* __restrict__ cl, T* __restrict__ phi,
+                               T* __restrict__ c, T* __restrict__ d, long long n, int interp, double a) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double f = (double)phi[i], s = (double)cs[i], l = (double)cl[i];
+        const double g = f * (1.0 - f);
+        const double h = (interp == 1) ? f * f * (3.0 - 2.0 * f) : f * f * f * (6.0 * f * f - 15.0 * f + 10.0);
+        const double p = h + a * (f - 0.5) * g * g;
+        c[i] = (T)(p * s + (1.0 - p) * l);
+        d[i] = (T)(s - l);
+    }
+}
+
+template <typename T>
+__global__ void batch_from_state(const T* __restrict__ phi, const T* __restrict__ c, const T* __restrict__ d,
+                                 T* __restrict__ cs, T* __restrict__ cl, long long n, int interp, double a) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double f = (double)phi[i], cc = (double)c[i], dd = (double)d[i];
+        const double g = f * (1.0 - f);
+        const double h = (interp == 1) ? f * f * (3.0 - 2.0 * f) : f * f * f * (6.0 * f * f - 15.0 * f + 10.0);
+        const double p = h + a * (f - 0.5) * g * g;
+        cs[i] = (T)(cc + (1.0 - p) * dd);
+        cl[i] = (T)(cc - p * dd);
+    }
+}
+
+namespace {
+
+double p_of_host(const pf_params& P, double f) {
+    const double g = f * (1.0 - f);
+    const double h = (P.interp == 1) ? f * f * (3.0 - 2.0 * f) : f * f * f * (6.0 * f * f - 15.0 * f + 10.0);
+    return h + P.a * (f - 0.5) * g * g;
+}
+
+int threads_for(int64_t n, int cpt) {
+    int nt = 128;
+    while (nt < 1024 && (int64_t)nt * cpt < n) nt *= 2;
+    return nt;
+}
+
+template <typename T>
+cudaError_t launch_group(int nt, const BatchArgs<T>& a, size_t smem, cudaStream_t s) {
+    switch (nt) {
+        case 128: batch_kernel<T, 128><<<a.count, 128, smem, s>>>(a); break;
+        case 256: batch_kernel<T, 256><<<a.count, 256, smem, s>>>(a); break;
+        case 512: batch_kernel<T, 512><<<a.count, 512, smem, s>>>(a); break;
+        default: batch_kernel<T, 1024><<<a.count, 1024, smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_smem_limits() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        const int mx = 227 * 1024;
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        err = e;
+    });
+    return err;
+}
+
+struct Group {
+    int nt;
+    int nmax;
+    std::vector<int> ids;
+    int* d_ids = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+template <typename T>
+struct BatchRun {
+    const pf_batch_desc& D;
+    cudaStream_t main;
+    std::string& err;
+    int64_t total = 0;
+    std::vector<int64_t> off;
+    std::vector<double> dt;
+    T *phi = nullptr, *c = nullptr, *d = nullptr;
+    BatchState* st = nullptr;
+    double *dv = nullptr, *ddt = nullptr;
+    std::vector<Group> groups;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    int64_t launches = 0;
+
+    BatchRun(const pf_batch_desc& d_, cudaStream_t s, std::string& e) : D(d_), main(s), err(e) {}
+    ~BatchRun() {
+        for (Group& g : groups) {
+            if (g.d_ids) cudaFree(g.d_ids);
+            if (g.stream) cudaStreamDestroy(g.stream);
+            if (g.done) cudaEventDestroy(g.done);
+        }
+        void* ptrs[] = {phi, c, d, st, dv, ddt};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        if (fork) cudaEventDestroy(fork);
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+    }
+
+    BatchArgs<T> args(const Group& g, int nsteps) const {
+        BatchArgs<T> a;
+        a.phi = phi; a.c = c; a.d = d; a.st = st; a.ids = g.d_ids; a.v = dv; a.dt = ddt;
+        a.count = (int)g.ids.size();
+        a.nsteps = nsteps;
+        a.check_every = (int)D.check_every;
+        a.tol = D.tol;
+        a.window = D.window;
+        const pf_params& P = D.params;
+        Consts<T>& C = a.C;
+        memset(&C, 0, sizeof(C));
+        C.dim = 1; C.interp = P.interp; C.lap = 3; C.mobility = P.mobility_mode;
+        C.dx = T(D.dx); C.inv_dx = T(1.0 / D.dx); C.inv_2dx = T(0.5 / D.dx); C.inv_dx2 = T(1.0 / (D.dx * D.dx));
+        C.H = T(P.H); C.sigma = T(P.sigma); C.inv_Mphi = T(1.0 / P.M_phi); C.D_s = T(P.D_s); C.D_l = T(P.D_l);
+        C.log_ke = T(std::log(P.k_e)); C.one_m_ke = T(1.0 - P.k_e); C.A = T(P.A); C.one_m_A = T(1.0 - P.A);
+        C.b = T(P.b); C.a = T(P.a); C.delta2 = T(P.delta * P.delta); C.G_theta = T(P.G_theta);
+        a.theta_ref = P.theta_ref; a.G_theta = P.G_theta; a.x0 = P.x0; a.c_inf = P.c_inf;
+        a.gphi = T(D.bc.dir_phi); a.gcs = T(D.bc.dir_cs); a.gcl = T(D.bc.dir_cl);
+        a.gmus = T(std::log(D.bc.dir_cs) - std::log(P.k_e));
+        a.gmul = T(std::log(D.bc.dir_cl));
+        const double pg = p_of_host(P, D.bc.dir_phi);
+        a.fc = T(pg * D.bc.dir_cs + (1.0 - pg) * D.bc.dir_cl);
+        a.fd = T(D.bc.dir_cs - D.bc.dir_cl);
+        return a;
+    }
+
+    cudaError_t issue(int nsteps) {
+        cudaError_t e = cudaEventRecord(fork, main);
+        for (Group& g : groups) {
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, fork, 0);
+            if (e == cudaSuccess) e = launch_group<T>(g.nt, args(g, nsteps), (size_t)6 * g.nmax * sizeof(T), g.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(main, g.done, 0);
+            launches += 1;
+        }
+        return e;
+    }
+
+    cudaError_t make_groups(int cpt) {
+        for (Group& g : groups) {
+            if (g.d_ids) cudaFree(g.d_ids);
+            if (g.stream) cudaStreamDestroy(g.stream);
+            if (g.done) cudaEventDestroy(g.done);
+        }
+        groups.clear();
+        std::map<int, Group> by;
+        for (int i = 0; i < D.n_instances; ++i) {
+            const int nt = threads_for(D.n[i], cpt);
+            Group& g = by[nt];
+            g.nt = nt;
+            g.nmax = std::max(g.nmax, (int)D.n[i]);
+            g.ids.push_back(i);
+        }
+        // largest instances first inside a group: the long CTAs start early
+        for (auto& kv : by) {
+            Group g = kv.second;
+            std::sort(g.ids.begin(), g.ids.end(), [&](int x, int y) { return D.n[x] > D.n[y]; });
+            cudaError_t e = cudaMalloc(&g.d_ids, g.ids.size() * sizeof(int));
+            if (e == cudaSuccess) e = cudaMemcpy(g.d_ids, g.ids.data(), g.ids.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+            groups.push_back(g);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+}  // namespace
+
+template <typename T>
+static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t main, std::string& err) {
+    BatchRun<T> B(D, main, err);
+    const int N = D.n_instances;
+    B.off.resize(N);
+    B.dt.resize(N);
+    for (int i = 0; i < N; ++i) {
+        B.off[i] = B.total;
+        B.total += D.n[i];
+    }
+    // time steps
+    pf_grid g1{1, {8, 1, 1}, D.dx};
+    double dts = 0;
+    pf_stable_dt(&g1, &D.params, &dts);
+    for (int i = 0; i < N; ++i) {
+        double dt = (D.dt && D.dt[i] > 0) ? D.dt[i] : 0.9 * dts;
+        if (!(D.dt && D.dt[i] > 0) && D.v_pull[i] > 0) dt = std::min(dt, 0.5 * D.dx / D.v_pull[i]);
+        if (!(dt > 0) || dt > dts * (1 + 1e-12) || D.v_pull[i] * dt >= D.dx) {
+            err = "invalid or unstable time step for instance " + std::to_string(i);
+            return PF_EINVAL;
+        }
+        B.dt[i] = dt;
+    }
+    const size_t fb = (size_t)B.total * sizeof(T);
+    cudaError_t e = cudaMalloc(&B.phi, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.c, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.d, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.st, N * sizeof(BatchState));
+    if (e == cudaSuccess) e = cudaMalloc(&B.dv, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&B.ddt, N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return PF_ENOMEM;
+    }
+    T *scs = nullptr, *scl = nullptr;
+    e = cudaMalloc(&scs, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&scl, fb);
+    if (e != cudaSuccess) {
+        if (scs) cudaFree(scs);
+        cudaGetLastError();
+        err = "device allocation failed";
+        return PF_ENOMEM;
+    }
+    std::vector<BatchState> hs(N);
+    for (int i = 0; i < N; ++i) {
+        hs[i] = BatchState{B.off[i], (int)D.n[i], 0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+    }
+    e = cudaMemcpyAsync(B.phi, D.phi0, fb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scs, D.cs0, fb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scl, D.cl0, fb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.st, hs.data(), N * sizeof(BatchState), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.dv, D.v_pull, N * sizeof(double), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.ddt, B.dt.data(), N * sizeof(double), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) {
+        batch_to_state<T><<<1216, 256, 0, main>>>(scs, scl, B.phi, B.c, B.d, B.total, D.params.interp, D.params.a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+    cudaFree(scs);
+    cudaFree(scl);
+    if (e == cudaSuccess) e = set_smem_limits<T>();
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&B.t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&B.t1);
+    if (e != cudaSuccess) {
+        err = std::string("batch set-up: ") + cudaGetErrorString(e);
+        return PF_ECUDA;
+    }
+
+    // autotune the cells per thread: time a short probe of every candidate on a
+    // scratch copy of the initial state
+    int cpt = D.cells_per_thread;
+    if (cpt == 0) {
+        T *bp = nullptr, *bc = nullptr, *bd = nullptr;
+        e = cudaMalloc(&bp, fb);
+        if (e == cudaSuccess) e = cudaMalloc(&bc, fb);
+        if (e == cudaSuccess) e = cudaMalloc(&bd, fb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bp, B.phi, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bc, B.c, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bd, B.d, fb, cudaMemcpyDeviceToDevice, main);
+        float best = 1e30f;
+        const int probe = 32;
+        for (int cand : {1, 2, 4, 8}) {
+            if (e != cudaSuccess) break;
+            bool ok = true;
+            for (int i = 0; i < N; ++i)
+                if (D.n[i] > (int64_t)1024 * cand) ok = false;
+            if (!ok) continue;
+            e = B.make_groups(cand);
+            if (e == cudaSuccess) e = cudaEventRecord(B.t0, main);
+            if (e == cudaSuccess) e = B.issue(probe);
+            if (e == cudaSuccess) e = cudaEventRecord(B.t1, main);
+            if (e == cudaSuccess) e = cudaEventSynchronize(B.t1);
+            float ms = 0;
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, B.t0, B.t1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                cpt = cand;
+            }
+            // restore the state the probe advanced
+            if (e == cudaSuccess) e = cudaMemcpyAsync(B.phi, bp, fb, cudaMemcpyDeviceToDevice, main);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(B.c, bc, fb, cudaMemcpyDeviceToDevice, main);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(B.d, bd, fb, cudaMemcpyDeviceToDevice, main);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(B.st, hs.data(), N * sizeof(BatchState), cudaMemcpyHostToDevice, main);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+        if (bp) cudaFree(bp);
+        if (bc) cudaFree(bc);
+        if (bd) cudaFree(bd);
+        if (e != cudaSuccess) {
+            err = std::string("batch autotune: ") + cudaGetErrorString(e);
+            return PF_ECUDA;
+        }
+        B.launches = 0;
+    }
+    e = B.make_groups(cpt);
+    if (e != cudaSuccess) {
+        err = std::string("batch groups: ") + cudaGetErrorString(e);
+        return PF_ECUDA;
+    }
+
+    // capture a chunk of launches as a CUDA graph and replay it
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+    for (int l = 0; l < D.launches_per_graph && e == cudaSuccess; ++l) e = B.issue((int)D.steps_per_launch);
+    cudaError_t e2 = cudaStreamEndCapture(main, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        err = std::string("batch graph: ") + cudaGetErrorString(e);
+        return PF_ECUDA;
+    }
+    const int64_t per_replay = D.steps_per_launch * D.launches_per_graph;
+    B.launches = 0;
+    float total_ms = 0;
+    int64_t done_steps = 0;
+    for (;;) {
+        e = cudaEventRecord(B.t0, main);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, main);
+        if (e == cudaSuccess) e = cudaEventRecord(B.t1, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), B.st, N * sizeof(BatchState), cudaMemcpyDeviceToHost, main);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+        if (e != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, B.t0, B.t1);
+        total_ms += ms;
+        B.launches += (int64_t)D.launches_per_graph * (int64_t)B.groups.size();
+        done_steps += per_replay;
+        bool all = true;
+        for (int i = 0; i < N; ++i)
+            if (!hs[i].converged) all = false;
+        if (all || done_steps >= D.max_steps) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        err = std::string("batch run: ") + cudaGetErrorString(e);
+        return PF_ECUDA;
+    }
+    for (int i = 0; i < N; ++i) {
+        if (R->k_v) R->k_v[i] = hs[i].k_last;
+        if (R->dkdt) R->dkdt[i] = hs[i].dkdt_last;
+        if (R->t) R->t[i] = (double)hs[i].step * B.dt[i];
+        if (R->steps) R->steps[i] = hs[i].step;
+        if (R->converged) R->converged[i] = hs[i].converged;
+    }
+    R->cells_per_thread = cpt;
+    R->launches = B.launches;
+    R->gpu_ms = total_ms;
+    if (R->phi && R->cs && R->cl) {
+        T *ocs = nullptr, *ocl = nullptr;
+        e = cudaMalloc(&ocs, fb);
+        if (e == cudaSuccess) e = cudaMalloc(&ocl, fb);
+        if (e == cudaSuccess) {
+            batch_from_state<T><<<1216, 256, 0, main>>>(B.phi, B.c, B.d, ocs, ocl, B.total, D.params.interp, D.params.a);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(R->phi, B.phi, fb, cudaMemcpyDeviceToHost, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(R->cs, ocs, fb, cudaMemcpyDeviceToHost, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(R->cl, ocl, fb, cudaMemcpyDeviceToHost, main);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+        if (ocs) cudaFree(ocs);
+        if (ocl) cudaFree(ocl);
+        if (e != cudaSuccess) {
+            err = std::string("batch fields: ") + cudaGetErrorString(e);
+            return PF_ECUDA;
+        }
+    }
+    return PF_OK;
+}
+
+int run_batch(const pf_batch_desc* D, pf_batch_result* R, void* stream, std::string& err) {
+    if (!D || !R) { err = "null argument"; return PF_EINVAL; }
+    const pf_params& P = D->params;
+    const int64_t nmax = (P.precision == PF_FP64) ? 4096 : 8192;
+    if (D->n_instances <= 0 || !D->n || !D->v_pull || !D->phi0 || !D->cs0 || !D->cl0) {
+        err = "empty batch or null array";
+        return PF_EINVAL;
+    }
+    for (int i = 0; i < D->n_instances; ++i) {
+        if (D->n[i] < 8 || D->n[i] > nmax) { err = "instance length outside 8.." + std::to_string(nmax); return PF_EINVAL; }
+        if (!(D->v_pull[i] >= 0) || !std::isfinite(D->v_pull[i])) { err = "negative or non-finite velocity"; return PF_EINVAL; }
+    }
+    if (!(D->dx > 0) || !(P.k_e > 0 && P.k_e < 1) || !(P.b > 0) || !(P.M_phi > 0) || !(P.H > 0) ||
+        !(P.sigma > 0) || !(P.D_s > 0) || !(P.D_l > 0) || !(P.c_inf > 0)) {
+        err = "invalid model parameters";
+        return PF_EINVAL;
+    }
+    if (P.precision != PF_FP32 && P.precision != PF_FP64) { err = "precision must be PF_FP32 or PF_FP64"; return PF_EINVAL; }
+    if (D->bc.lo[0] != PF_BC_NOFLUX || D->bc.hi[0] != PF_BC_DIRICHLET) {
+        err = "batch instances need a no-flux cold end and a Dirichlet hot end";
+        return PF_EINVAL;
+    }
+    if (!(D->bc.dir_cs > 0) || !(D->bc.dir_cl > 0)) { err = "Dirichlet concentrations must be positive"; return PF_EINVAL; }
+    if (D->steps_per_launch <= 0 || D->launches_per_graph <= 0 || D->check_every <= 0 || D->max_steps <= 0 ||
+        D->steps_per_launch > (1 << 30)) {
+        err = "steps_per_launch, launches_per_graph, check_every and max_steps must be positive";
+        return PF_EINVAL;
+    }
+    const int cpt = D->cells_per_thread;
+    if (cpt != 0 && cpt != 1 && cpt != 2 && cpt != 4 && cpt != 8) { err = "cells_per_thread must be 0, 1, 2, 4 or 8"; return PF_EINVAL; }
+    if (cpt != 0)
+        for (int i = 0; i < D->n_instances; ++i)
+            if (D->n[i] > (int64_t)1024 * cpt) { err = "cells_per_thread too small for the longest instance"; return PF_EINVAL; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (P.precision == PF_FP64) return run_batch_T<double>(*D, R, s, err);
+    return run_batch_T<float>(*D, R, s, err);
+}
+
+}  // namespace pf
+
+namespace {
+thread_local std::string g_batch_error;
+}
+
+extern "C" int pf_run_batch(const pf_batch_desc* desc, pf_batch_result* res, void* stream) {
+    g_batch_error.clear();
+    const int rc = pf::run_batch(desc, res, stream, g_batch_error);
+    if (rc != PF_OK) pf::set_create_error(g_batch_error);
+    return rc;
+}

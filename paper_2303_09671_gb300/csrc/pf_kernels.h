@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <cmath>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace pf {
@@ -58,6 +59,8 @@ cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& o
 // (phi, c_s, c_l) of the caller's precision <-> the device state (phi, c, d[, c_lo])
 cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* cs, const void* cl,
                             const Fields& out, cudaStream_t s);
+void set_create_error(const std::string& msg);
+
 cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
                               cudaStream_t s);
 

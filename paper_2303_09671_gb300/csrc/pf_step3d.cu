@@ -58,7 +58,11 @@ struct Tile3 {
 };
 
 // face fluxes from the face state; nrm = normal differences (R - L) of
-// {phi, Y, mu_s, mu_l} times 1/dx, t1, t2 = the two transverse components
+// {phi, Y, mu_s, mu_l} times 1/dx, t1, t2 = the two transverse components.
+// With T_i = M_i [d_a mu_i (|g_t|^2 + delta^2) - g_a (g_t . grad_t mu_i)] (the
+// tangential fluxes times 1/r) and w_s + w_l = 1, p w_s - (1-p) w_l = a(phi):
+//   F_c = r [q g_a (g . grad Y) + p T_s + (1-p) T_l + (1-A) d phidot g_a a(phi)]
+//   F_d = r [T_s - T_l + (1-A) d phidot g_a]
 template <typename T>
 __device__ __forceinline__ V2<T> face3(const Consts<T>& C, T phiL, T phiR, V2<T> cL, V2<T> cR,
                                        T pdL, T pdR, V4<T> nrm, V4<T> t1, V4<T> t2) {
@@ -68,26 +72,22 @@ __device__ __forceinline__ V2<T> face3(const Consts<T>& C, T phiL, T phiR, V2<T>
     const T d = cs - cl;
     const T pdot = T(0.5) * (pdL + pdR);
     const T p = p_of(C, f);
+    const T omp = T(1) - p;
     const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
-    const T bMlp = C.b * Ml * p;
-    const T Msq = Ms * (T(1) - p);
-    const T iMbar = frcp(Msq + bMlp);
-    const T q = Ms * Ml * (C.b * p + T(1) - p) * iMbar;
-    const T ws = Msq * iMbar;
-    const T wl = bMlp * iMbar;
+    const T bMl = C.b * Ml;
+    const T iMbar = frcp(Ms * omp + bMl * p);
     const T gt2d = t1.x * t1.x + t2.x * t2.x + C.delta2;
-    const T dYt = t1.x * t1.y + t2.x * t2.y;
-    const T dst = t1.x * t1.z + t2.x * t2.z;
-    const T dlt = t1.x * t1.w + t2.x * t2.w;
     const T ga = nrm.x;
     const T r = frcp(ga * ga + gt2d);
-    const T normal = q * ga * (ga * nrm.y + dYt) * r;
-    const T at = C.one_m_A * d * pdot * ga * r;
-    const T Fs = normal + Ms * (nrm.z * gt2d - ga * dst) * r + at * ws;
-    const T Fl = normal + Ml * (nrm.w * gt2d - ga * dlt) * r - at * wl;
+    const T dY = ga * nrm.y + t1.x * t1.y + t2.x * t2.y;
+    const T Ts = Ms * (nrm.z * gt2d - ga * (t1.x * t1.z + t2.x * t2.z));
+    const T Tl = Ml * (nrm.w * gt2d - ga * (t1.x * t1.w + t2.x * t2.w));
+    const T at = C.one_m_A * d * pdot * ga;
+    const T q = Ms * Ml * (C.b * p + omp) * iMbar;
+    const T afn = (Ms - bMl) * p * omp * iMbar;
     V2<T> out;
-    out.x = p * Fs + (T(1) - p) * Fl;   // F_c
-    out.y = Fs - Fl;                    // F_d
+    out.x = r * (q * ga * dY + p * Ts + omp * Tl + at * afn);   // F_c
+    out.y = r * (Ts - Tl + at);                                  // F_d
     return out;
 }
 

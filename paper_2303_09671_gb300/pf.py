@@ -11,8 +11,6 @@ By default the handle runs on torch's current CUDA stream.
 from __future__ import annotations
 
 import ctypes
-import math
-import os
 import threading
 
 import numpy as np
@@ -51,6 +49,24 @@ class pf_params(ctypes.Structure):
     ] + [("shift", ctypes.c_int)]
 
 
+class pf_batch_desc(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int), ("n", ctypes.POINTER(ctypes.c_int64)),
+                ("v_pull", ctypes.POINTER(ctypes.c_double)), ("dt", ctypes.POINTER(ctypes.c_double)),
+                ("phi0", ctypes.c_void_p), ("cs0", ctypes.c_void_p), ("cl0", ctypes.c_void_p),
+                ("dx", ctypes.c_double), ("bc", pf_bc), ("params", pf_params),
+                ("max_steps", ctypes.c_int64), ("steps_per_launch", ctypes.c_int64),
+                ("launches_per_graph", ctypes.c_int), ("check_every", ctypes.c_int64),
+                ("window", ctypes.c_double), ("tol", ctypes.c_double), ("cells_per_thread", ctypes.c_int)]
+
+
+class pf_batch_result(ctypes.Structure):
+    _fields_ = [("k_v", ctypes.POINTER(ctypes.c_double)), ("dkdt", ctypes.POINTER(ctypes.c_double)),
+                ("t", ctypes.POINTER(ctypes.c_double)), ("steps", ctypes.POINTER(ctypes.c_int64)),
+                ("converged", ctypes.POINTER(ctypes.c_int)), ("phi", ctypes.c_void_p),
+                ("cs", ctypes.c_void_p), ("cl", ctypes.c_void_p), ("cells_per_thread", ctypes.c_int),
+                ("launches", ctypes.c_int64), ("gpu_ms", ctypes.c_double)]
+
+
 # exported symbols and their signatures (the header include/pf.h declares the same set)
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -66,6 +82,7 @@ _SIGS = {
     "pf_set_clock": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64]),
     "pf_stable_dt": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_params),
                                     ctypes.POINTER(ctypes.c_double)]),
+    "pf_run_batch": (ctypes.c_int, [ctypes.POINTER(pf_batch_desc), ctypes.POINTER(pf_batch_result), _VP]),
     "pf_last_error": (ctypes.c_char_p, [_VP]),
     "pf_destroy": (None, [_VP]),
 }
@@ -223,3 +240,52 @@ class Sim:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt=None,
+              max_steps=100000, steps_per_launch=500, launches_per_graph=4, check_every=100,
+              window=1.0, tol=1e-8, cells_per_thread=0, want_fields=False, stream=None):
+    """pf_run_batch: many 1D pulled fronts in one persistent launch per chunk.
+
+    pr: shared 1D parameters (workloads.pulled_front_1d style; n, v_pull, dt and
+    shift are ignored); lengths, v_pull (and dt) per instance; phi0, cs0, cl0
+    packed initial fields.  Returns a dict of per-instance arrays.
+    """
+    N = len(lengths)
+    dtype = np.float64 if precision == "fp64" else np.float32
+    n_arr = np.ascontiguousarray(lengths, dtype=np.int64)
+    v_arr = np.ascontiguousarray(v_pull, dtype=np.float64)
+    dt_arr = np.ascontiguousarray(dt if dt is not None else np.zeros(N), dtype=np.float64)
+    fields = [np.ascontiguousarray(a, dtype=dtype) for a in (phi0, cs0, cl0)]
+    total = int(n_arr.sum())
+    for a in fields:
+        if a.shape != (total,):
+            raise ValueError("packed fields must have sum(lengths) entries")
+    g, b, p = make_structs(dict(pr, n=(8,), shift=False, v_pull=0.0), precision)
+    D = pf_batch_desc()
+    D.n_instances = N
+    D.n = n_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    D.v_pull = v_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    D.dt = dt_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    D.phi0, D.cs0, D.cl0 = (a.ctypes.data for a in fields)
+    D.dx = float(pr["dx"])
+    D.bc = b
+    D.params = p
+    D.max_steps, D.steps_per_launch, D.launches_per_graph = int(max_steps), int(steps_per_launch), int(launches_per_graph)
+    D.check_every, D.window, D.tol, D.cells_per_thread = int(check_every), float(window), float(tol), int(cells_per_thread)
+    out = dict(k_v=np.zeros(N), dkdt=np.zeros(N), t=np.zeros(N), steps=np.zeros(N, np.int64),
+               converged=np.zeros(N, np.int32))
+    R = pf_batch_result()
+    R.k_v = out["k_v"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    R.dkdt = out["dkdt"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    R.t = out["t"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    R.steps = out["steps"].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    R.converged = out["converged"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    if want_fields:
+        for k in ("phi", "cs", "cl"):
+            out[k] = np.zeros(total, dtype=dtype)
+        R.phi, R.cs, R.cl = (out[k].ctypes.data for k in ("phi", "cs", "cl"))
+    s = _current_stream() if stream is None else stream
+    _check(lib().pf_run_batch(ctypes.byref(D), ctypes.byref(R), _VP(s)), None)
+    out.update(cells_per_thread=R.cells_per_thread, launches=R.launches, gpu_ms=R.gpu_ms)
+    return out

@@ -1,0 +1,96 @@
+"""Batched 1D pulled fronts (pf_run_batch) against the FP64 oracle and the
+single-instance path."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09671_gb300 import workloads as wl
+from paper_2303_09671_gb300 import pf
+
+from conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def batch_inputs(lengths, vs, A=1.0, b=1.0, dx=0.5):
+    prs, phis, css, cls = [], [], [], []
+    for n, v in zip(lengths, vs):
+        pr, phi, cs, cl = wl.pulled_front_1d(N=n, dx=dx, V=v, A=A, b=b, front_cell=n // 4)
+        prs.append(pr)
+        phis.append(phi)
+        css.append(cs)
+        cls.append(cl)
+    return prs, np.concatenate(phis), np.concatenate(css), np.concatenate(cls)
+
+
+def oracle_runs(prs, lengths, phis, css, cls, dts, nsteps):
+    out, o = [], 0
+    for pr, n, dt in zip(prs, lengths, dts):
+        st = oracle.State(dict(pr, dt=dt), phis[o:o + n], css[o:o + n], cls[o:o + n])
+        st.step(nsteps)
+        out.append(st)
+        o += n
+    return out
+
+
+def test_batch_fp64_matches_oracle():
+    """Four instances of different lengths and velocities, 300 steps (3 graph
+    replays of 2 launches x 50 steps) with window shifts."""
+    lengths = [64, 200, 333, 512]
+    vs = [0.05, 0.1, 0.2, 0.3]
+    prs, phi, cs, cl = batch_inputs(lengths, vs)
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    res = pf.run_batch(prs[0], lengths, vs, phi, cs, cl, precision="fp64", dt=dts, max_steps=300,
+                       steps_per_launch=50, launches_per_graph=2, check_every=100, tol=-1.0,
+                       want_fields=True)
+    assert (res["steps"] == 300).all() and not res["converged"].any()
+    ref = oracle_runs(prs, lengths, phi, cs, cl, dts, 300)
+    o = 0
+    for n, st in zip(lengths, ref):
+        assert st.clock.shifts > 0
+        for a, b_ in ((res["phi"][o:o + n], st.phi), (res["cs"][o:o + n], st.cs), (res["cl"][o:o + n], st.cl)):
+            assert rel_err(a, b_) <= 1e-11, rel_err(a, b_)
+        o += n
+
+
+@pytest.mark.parametrize("cpt", [1, 2, 8])
+def test_batch_fp32_matches_single_instance_path(cpt):
+    lengths = [96, 300, 700]
+    vs = [0.1, 0.2, 0.4]
+    prs, phi, cs, cl = batch_inputs(lengths, vs)
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    res = pf.run_batch(prs[0], lengths, vs, phi, cs, cl, precision="fp32", dt=dts, max_steps=400,
+                       steps_per_launch=100, launches_per_graph=2, check_every=100, tol=-1.0,
+                       want_fields=True, cells_per_thread=cpt)
+    o = 0
+    for pr, n, dt in zip(prs, lengths, dts):
+        with pf.Sim(dict(pr, dt=dt), "fp32") as s:
+            s.set_fields(phi[o:o + n], cs[o:o + n], cl[o:o + n])
+            s.step(400)
+            g = s.get_fields()
+        assert np.abs(res["phi"][o:o + n] - g[0]).max() <= 1e-5
+        assert rel_err(res["cs"][o:o + n], g[1]) <= 1e-5 and rel_err(res["cl"][o:o + n], g[2]) <= 1e-5
+        o += n
+
+
+def test_batch_autotunes_and_converges():
+    """A small k(V) sweep run to its steady states: every instance converges,
+    k_v grows with V (less partitioning at higher speed) and stays below 1."""
+    lengths = [512, 1024, 768]
+    vs = [2.0, 0.5, 1.0]
+    prs, phi, cs, cl = batch_inputs(lengths, vs)
+    res = pf.run_batch(prs[0], lengths, vs, phi, cs, cl, precision="fp32", max_steps=400000,
+                       steps_per_launch=1000, launches_per_graph=4, check_every=200, window=2.0,
+                       tol=1e-6)
+    assert res["cells_per_thread"] in (1, 2, 4, 8)
+    assert res["converged"].all(), res
+    k = dict(zip(vs, res["k_v"]))
+    assert 0 < k[0.5] < k[1.0] < k[2.0] < 1.0, k
+
+
+def test_batch_rejects_invalid():
+    prs, phi, cs, cl = batch_inputs([64], [0.1])
+    with pytest.raises(pf.PFError):
+        pf.run_batch(prs[0], [4], [0.1], phi[:4], cs[:4], cl[:4])
+    with pytest.raises(pf.PFError):
+        pf.run_batch(prs[0], [64], [-1.0], phi, cs, cl)
