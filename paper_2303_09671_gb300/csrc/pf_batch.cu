@@ -338,18 +338,34 @@ cudaError_t launch_group(int nt, const BatchArgs<T>& a, size_t smem, cudaStream_
     return cudaGetLastError();
 }
 
+// raise each instantiation's dynamic shared-memory limit to what the device
+// allows next to the kernel's static shared memory
+template <typename K>
+cudaError_t raise_smem(K kern, int optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 template <typename T>
-cudaError_t set_smem_limits() {
+cudaError_t set_smem_limits(size_t* max_dynamic) {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
+    static size_t limit = 0;
     std::call_once(once, [] {
-        const int mx = 227 * 1024;
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 128>, optin);
+        if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 256>, optin);
+        if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 512>, optin);
+        if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 1024>, optin);
+        limit = (size_t)optin - 1024;   // static part: reduction scratch and flag
         err = e;
     });
+    *max_dynamic = limit;
     return err;
 }
 
@@ -523,7 +539,16 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
     if (e == cudaSuccess) e = cudaStreamSynchronize(main);
     cudaFree(scs);
     cudaFree(scl);
-    if (e == cudaSuccess) e = set_smem_limits<T>();
+    size_t max_dyn = 0;
+    if (e == cudaSuccess) e = set_smem_limits<T>(&max_dyn);
+    if (e == cudaSuccess) {
+        int64_t nbig = 0;
+        for (int i = 0; i < N; ++i) nbig = std::max(nbig, (int64_t)D.n[i]);
+        if ((size_t)6 * nbig * sizeof(T) > max_dyn) {
+            err = "longest instance does not fit in shared memory";
+            return PF_EINVAL;
+        }
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&B.t0);
     if (e == cudaSuccess) e = cudaEventCreate(&B.t1);
