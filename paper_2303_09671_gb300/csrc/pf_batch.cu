@@ -681,6 +681,34 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
     return PF_OK;
 }
 
+// Runs on a private non-blocking stream forked from the caller's (which may be
+// the legacy default stream, not capturable) and joined back at the end.
+template <typename T>
+static int run_batch_forked(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t caller, std::string& err) {
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(work, ev, 0);
+    int rc = PF_ECUDA;
+    if (e == cudaSuccess) {
+        rc = run_batch_T<T>(D, R, work, err);
+        cudaError_t e2 = cudaEventRecord(ev, work);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(caller, ev, 0);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(work);
+        if (rc == PF_OK && e2 != cudaSuccess) {
+            err = std::string("batch join: ") + cudaGetErrorString(e2);
+            rc = PF_ECUDA;
+        }
+    } else {
+        err = std::string("batch stream: ") + cudaGetErrorString(e);
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (work) cudaStreamDestroy(work);
+    return rc;
+}
+
 int run_batch(const pf_batch_desc* D, pf_batch_result* R, void* stream, std::string& err) {
     if (!D || !R) { err = "null argument"; return PF_EINVAL; }
     const pf_params& P = D->params;
@@ -715,8 +743,8 @@ int run_batch(const pf_batch_desc* D, pf_batch_result* R, void* stream, std::str
         for (int i = 0; i < D->n_instances; ++i)
             if (D->n[i] > (int64_t)1024 * cpt) { err = "cells_per_thread too small for the longest instance"; return PF_EINVAL; }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (P.precision == PF_FP64) return run_batch_T<double>(*D, R, s, err);
-    return run_batch_T<float>(*D, R, s, err);
+    if (P.precision == PF_FP64) return run_batch_forked<double>(*D, R, s, err);
+    return run_batch_forked<float>(*D, R, s, err);
 }
 
 }  // namespace pf
