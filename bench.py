@@ -172,7 +172,7 @@ def kv_sweep_inputs(n_inst=256, seed=4):
     prs, phis, css, cls = [], [], [], []
     for n, v in zip(lengths, vs):
         pr, phi, cs, cl = wl.pulled_front_1d(N=int(n), dx=0.5, V=float(v), G_theta=5.25e-3,
-                                             front_cell=int(n) // 4, A=1.0, b=1.0)
+                                             front_cell=128, A=1.0, b=1.0)
         prs.append(pr)
         phis.append(phi)
         css.append(cs)

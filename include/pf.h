@@ -167,7 +167,8 @@ int pf_stable_dt(const pf_grid* grid, const pf_params* params, double* dt);
  * persistent launch per chunk of steps, replayed as a CUDA graph.
  *
  * Every instance is a 1D directional-solidification problem: frozen
- * temperature theta(x,t) = theta_ref - G_theta ((x - x0) - v t) (Eq. ds1), no-flux
+ * temperature theta(x,t) = theta_ref - G_theta ((x - x0) - v t) (Eq. ds1, with
+ * theta_ref, G_theta and x0 of `params` shared by all instances), no-flux
  * cold end, fixed hot end (bc.dir_*), moving window (Sec. "Numerical
  * technique"), and the shared model parameters of `params` (params.v_pull,
  * params.dt and params.shift are ignored; precision FP32 or FP64).
@@ -189,7 +190,9 @@ typedef struct {
     int launches_per_graph;    /* launches captured in one CUDA graph (> 0) */
     int64_t check_every;       /* steps between k_v evaluations (> 0) */
     double window;             /* minimum time between the two k_v samples of a rate */
-    double tol;                /* converged when |dk_v/dt| < tol */
+    double tol;                /* converged when |dk_v/dt| < tol ...                  */
+    double min_travel;         /* ... and the temperature has been pulled >= min_travel
+                                  (units of W), i.e. t >= min_travel / v */
     int cells_per_thread;      /* 1, 2, 4 or 8; 0 = autotune */
 } pf_batch_desc;
 

@@ -52,7 +52,7 @@ struct BatchArgs {
     int count;
     int nsteps;
     int check_every;
-    double tol, window;
+    double tol, window, min_travel;
     Consts<T> C;        // shared model parameters (dt unused; per instance)
     double theta_ref, G_theta, x0, c_inf;
     T gphi, gcs, gcl, gmus, gmul;   // Dirichlet (hot end) ghost
@@ -255,7 +255,7 @@ batch_kernel(BatchArgs<T> a) {
                 k_last = k;
                 if (tn - t_prev >= a.window) {
                     dkdt_last = fabs(k - k_prev) / (tn - t_prev);
-                    s_done = (t_prev > 0.0 && dkdt_last < a.tol) ? 1 : 0;
+                    s_done = (t_prev > 0.0 && dkdt_last < a.tol && v * tn >= a.min_travel) ? 1 : 0;
                     k_prev = k;
                     t_prev = tn;
                 }
@@ -416,6 +416,7 @@ struct BatchRun {
         a.check_every = (int)D.check_every;
         a.tol = D.tol;
         a.window = D.window;
+        a.min_travel = D.min_travel;
         const pf_params& P = D.params;
         Consts<T>& C = a.C;
         memset(&C, 0, sizeof(C));

