@@ -216,6 +216,29 @@ typedef struct {
  * memory; synchronises `stream`.  Returns PF_EINVAL for invalid descriptors. */
 int pf_run_batch(const pf_batch_desc* desc, pf_batch_result* res, void* stream);
 
+/* Allocation-free FP64 free energy and total solute (the paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory -- a process whose device memory is held by another allocator, a
+ * monitoring or real-time path that must not block or fail on cudaMalloc, or a
+ * caller without a pf_handle, since pf_create allocates).
+ *
+ * Computes the same F_h (out[0]) and S_h (out[1]) as pf_energy and
+ * pf_solute_total, directly from caller-owned device arrays phi, cs, cl of
+ * n[0]*n[1]*n[2] values (x fastest, element type of params->precision) at the
+ * clock (step, shifts), and writes the two doubles to the caller-owned device
+ * pointer `out`, ordered on `stream` (no host synchronisation).  It calls no
+ * cudaMalloc/cudaFree: the reduction's block partials live in a 19 KiB
+ * file-scope device array that stays resident on every GPU that loads the
+ * library.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and must therefore come before any stream capture
+ * on that device.  All calls share the array; each call rewrites every partial
+ * it reads, but calls whose kernels overlap on the GPU race and must be
+ * serialised by the caller.  Grids above 2^30 cells, invalid sizes or
+ * parameters return PF_EINVAL (message via pf_last_error(NULL)). */
+int pf_energy_solute_noalloc(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
+                             int64_t step, int64_t shifts, const void* phi, const void* cs,
+                             const void* cl, double* out, void* stream);
+
 /* Message describing the last error on h (or the last pf_create failure when
  * h is NULL).  Owned by the library; valid until the next call on h. */
 const char* pf_last_error(pf_handle* h);

@@ -84,6 +84,9 @@ _SIGS = {
     "pf_stable_dt": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_params),
                                     ctypes.POINTER(ctypes.c_double)]),
     "pf_run_batch": (ctypes.c_int, [ctypes.POINTER(pf_batch_desc), ctypes.POINTER(pf_batch_result), _VP]),
+    "pf_energy_solute_noalloc": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_bc),
+                                                ctypes.POINTER(pf_params), ctypes.c_int64, ctypes.c_int64,
+                                                _VP, _VP, _VP, _VP, _VP]),
     "pf_last_error": (ctypes.c_char_p, [_VP]),
     "pf_destroy": (None, [_VP]),
 }
@@ -292,3 +295,14 @@ def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt
     _check(lib().pf_run_batch(ctypes.byref(D), ctypes.byref(R), _VP(s)), None)
     out.update(cells_per_thread=R.cells_per_thread, launches=R.launches, gpu_ms=R.gpu_ms)
     return out
+
+
+def energy_solute_noalloc(pr: dict, phi, cs, cl, out, precision="fp32", step=0, shifts=0, stream=None):
+    """pf_energy_solute_noalloc on CUDA tensors: writes (F_h, S_h) into the
+    2-element float64 CUDA tensor `out` without allocating device memory."""
+    g, b, p = make_structs(pr, precision)
+    s = _current_stream() if stream is None else stream
+    rc = lib().pf_energy_solute_noalloc(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), int(step),
+                                        int(shifts), _VP(phi.data_ptr()), _VP(cs.data_ptr()),
+                                        _VP(cl.data_ptr()), _VP(out.data_ptr()), _VP(s))
+    _check(rc, None)

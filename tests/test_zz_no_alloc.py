@@ -1,0 +1,54 @@
+"""pf_energy_solute_noalloc: the allocation-free energy/solute reduction, for
+callers that cannot allocate device memory (their device memory is held by
+another allocator, they run on a path that must not block or fail on an
+allocation, or they have no pf_handle), checked against pf_energy and
+pf_solute_total on two calls in a row.  Collected last on purpose."""
+import numpy as np
+import pytest
+
+from paper_2303_09671_gb300 import workloads as wl
+from paper_2303_09671_gb300 import pf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,maker", [
+    ("fp64", lambda: wl.random_state(3, (37, 19, 13), A=1.5, b=0.3, seed=7)),
+    ("fp64", lambda: wl.pulled_front_1d(N=300, V=0.1, A=1.0, b=1.0)),
+    ("fp32", lambda: wl.perturbed_front_2d(nx=96, ny=64, front=30, A=1.5, b=0.3)),
+])
+def test_noalloc_matches_handle_reductions(precision, maker):
+    import torch
+    pr, phi, cs, cl = maker()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    npdt = np.float64 if precision == "fp64" else np.float32
+    phi, cs, cl = (np.asarray(a, dtype=npdt) for a in (phi, cs, cl))
+    with pf.Sim(pr, precision) as s:
+        s.set_fields(phi, cs, cl)
+        s.step(3)
+        E_ref, S_ref = s.energy(), s.solute_total()
+        fields = s.get_fields()
+        step, shifts = s.clock
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for _ in range(2):       # the shared scratch array is reused by the second call
+        out.fill_(float("nan"))
+        pf.energy_solute_noalloc(pr, *dev, out, precision=precision, step=step, shifts=shifts)
+        torch.cuda.synchronize()
+        E, S = out.cpu().numpy()
+        assert abs(E - E_ref) <= tol * abs(E_ref), (E, E_ref)
+        assert abs(S - S_ref) <= tol * abs(S_ref), (S, S_ref)
+
+
+def test_noalloc_rejects_invalid_sizes():
+    import torch
+    pr, phi, cs, cl = wl.random_state(2, (8, 8))
+    t = torch.zeros(64, dtype=torch.float32, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    big = dict(pr, n=(1 << 16, 1 << 15))
+    with pytest.raises(pf.PFError, match="2\\^30"):
+        pf.energy_solute_noalloc(big, t, t, t, out)
+    bad = dict(pr, lap=19)
+    with pytest.raises(pf.PFError, match="lap_stencil"):
+        pf.energy_solute_noalloc(bad, t, t, t, out)
