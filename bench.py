@@ -4,9 +4,9 @@
 Workload (one step = one forward-Euler step of the whole hot path over the
 grid): 3D 256^3 FP32, spherical solid seed of radius 20 cells with seeded
 surface noise, k_e = 0.1, undercooling 0.5 of the freezing range, D_s/D_l =
-1e-4, dx = W/2, 19-point Laplacian, no-flux box.  The state (3 x 64 MiB read
-and 3 x 64 MiB written per step) is larger than the 129 MB L2, so no flush is
-needed between steps.
+1e-4, dx = W/2, 19-point Laplacian, no-flux box.  The device state (phi, c,
+d = c_s - c_l and the compensation word of c: 4 x 64 MiB, read and written
+every step) is larger than the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -46,7 +46,9 @@ def workload(n):
 def config(n, steps_note):
     return {"workload": f"3D sphere seed {n}^3 FP32 (k_e=0.1, u=0.5, D_s/D_l=1e-4, dx=W/2, "
                         f"19-pt, no-flux, A={PARAMS['A']}, b={PARAMS['b']})",
-            "grid": [n, n, n], "dtype": "f32", "cache": "state 201 MB > L2 (129 MB), no flush",
+            "grid": [n, n, n], "dtype": "f32",
+            "cache": (f"state {16 * n ** 3 / 1e6:.0f} MB (phi, c, d, c_lo) "
+                      + ("> L2 (129 MB), no flush" if 16 * n ** 3 > 129e6 else "fits in L2 (129 MB)")),
             "scaling_unit": "one independent grid per rank", **steps_note}
 
 
@@ -57,6 +59,33 @@ def config(n, steps_note):
 OPS_PER_CELL_UPDATE = 509
 BYTES_PER_CELL_UPDATE = 24          # FP32 read + write of phi, c_s, c_l (algorithmic)
 SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step3d_kernel
+# launch from an ncu capture, per cell-update, and the SHA-256 of the kernel
+# sources the capture ran.  The figure is reported as null as soon as those
+# sources differ from the ones captured.
+TRAFFIC_CAPTURE = {
+    "bytes_per_cell_update": (181.988864e6 + 143.170560e6) / 224 ** 3,
+    "captured_grid": 224,
+    "sources": ("pf_step3d.cu", "pf_internal.cuh", "pf_kernels.h"),
+    "sha256": ("0f62f2fbe9700dd8aaa9676e1447eb602669d994a5b2962129b6c464cf4acf58",
+               "ffdc389efafe89f3717680b7f2777ee9aaf7cd0de04f3e905dcde7f6b84b7089",
+               "6f2b278b5cc421adbf544bb59fc1386d67b011600adc02e65bcfb5f7ad7347a0"),
+}
+
+
+def step3d_traffic(cells):
+    """DRAM bytes per launch at `cells` scaled from the capture, or None if stale."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2303_09671_gb300", "csrc")
+    for name, want in zip(TRAFFIC_CAPTURE["sources"], TRAFFIC_CAPTURE["sha256"]):
+        try:
+            with open(os.path.join(csrc, name), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != want:
+                    return None
+        except OSError:
+            return None
+    return TRAFFIC_CAPTURE["bytes_per_cell_update"] * cells
 
 
 def load_peaks():
@@ -325,13 +354,18 @@ def main():
         # FP32 ALU peak: every lane issuing one FMA (2 operations) per clock
         alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         achieved_tops = OPS_PER_CELL_UPDATE * cells / launch_s / 1e12
+        traffic = step3d_traffic(cells)
+        traffic_note = (f"ncu DRAM bytes of one launch at {TRAFFIC_CAPTURE['captured_grid']}^3, "
+                        f"scaled by cells to {n}^3" if traffic is not None else
+                        "kernel sources changed since the capture")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config(n, {"parallelism": f"independent grid per GPU x{world}"}),
             "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": achieved_tops / alu_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved_tops / alu_peak, "traffic": traffic,
+                         "traffic_note": traffic_note,
                          "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_mhz:.0f} MHz",
                          "kernel": "step3d_kernel<float,32,8,4>",
                          "ops_per_cell_update": OPS_PER_CELL_UPDATE},

@@ -21,8 +21,11 @@
  *   Euler (Sec. "Numerical technique").
  *
  * Memory and ownership: a pf_handle owns every device buffer it allocates
- * (two ping-pong copies of phi, c_s, c_l in the chosen precision, SoA, x
- * fastest, plus reduction scratch).  Pointers passed to any call are borrowed
+ * (two ping-pong copies of the state in the chosen precision, SoA, x
+ * fastest: phi, the mixture concentration c = p(phi) c_s + (1 - p(phi)) c_l,
+ * the difference d = c_s - c_l and, in FP32, the low word of a compensated
+ * c; plus reduction scratch).  pf_set_fields / pf_get_fields convert between
+ * the caller's (phi, c_s, c_l) and this state.  Pointers passed to any call are borrowed
  * for the duration of that call only.  All device work is ordered on the
  * CUDA stream given to pf_create (a cudaStream_t passed as void*, NULL = the
  * legacy default stream); calls that return host values synchronise that
