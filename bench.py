@@ -367,7 +367,7 @@ def main():
                          "unit": "TFLOP/s", "frac": achieved_tops / alu_peak, "traffic": traffic,
                          "traffic_note": traffic_note,
                          "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_mhz:.0f} MHz",
-                         "kernel": "step3d_kernel<float,32,8,4>",
+                         "kernel": "step3d_kernel<float,32,16,19-point>",
                          "ops_per_cell_update": OPS_PER_CELL_UPDATE},
             "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved_gbs / hbm_peak, "peak_source": how,

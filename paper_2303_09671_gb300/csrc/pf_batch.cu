@@ -425,6 +425,7 @@ struct BatchRun {
         C.H = T(P.H); C.sigma = T(P.sigma); C.inv_Mphi = T(1.0 / P.M_phi); C.D_s = T(P.D_s); C.D_l = T(P.D_l);
         C.log_ke = T(std::log(P.k_e)); C.one_m_ke = T(1.0 - P.k_e); C.A = T(P.A); C.one_m_A = T(1.0 - P.A);
         C.b = T(P.b); C.a = T(P.a); C.delta2 = T(P.delta * P.delta); C.G_theta = T(P.G_theta);
+        set_coefficients(C);
         a.theta_ref = P.theta_ref; a.G_theta = P.G_theta; a.x0 = P.x0; a.c_inf = P.c_inf;
         a.gphi = T(D.bc.dir_phi); a.gcs = T(D.bc.dir_cs); a.gcl = T(D.bc.dir_cl);
         a.gmus = T(std::log(D.bc.dir_cs) - std::log(P.k_e));

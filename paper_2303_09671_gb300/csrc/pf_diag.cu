@@ -1,6 +1,6 @@
 // pf_diag.cu -- FP64 diagnostics (discrete free energy, total solute, front,
 // c_max), the 1D moving-window shift and the conversions between the
-// caller's (phi, c_s, c_l) and the device state (phi, c, d).
+// caller's (phi, c_s, c_l) and the device state (phi, c, d[, c_lo]).
 //
 // Reductions are deterministic: a fixed grid of DIAG_BLOCKS blocks writes one
 // partial per block (warp-shuffle tree inside the block), and a single block
@@ -213,6 +213,81 @@ __global__ void to_state_kernel(const T* __restrict__ phi, const T* __restrict__
     }
 }
 
+// FP32 input: the conversion in FP32 arithmetic (the FP64 units of a GB300
+// are a small fraction of its FP32 rate).  p(phi) is evaluated in FP32 and
+// c = c_l + p (c_s - c_l) is kept exactly as an unevaluated sum hi + lo of
+// two floats: c_s - c_l and c_l + p d by TwoSum, p d by an FMA-based exact
+// product (Knuth; Dekker), so the stored (c, c_lo) carries ~2^-48 relative
+// error with respect to that p.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+to_state_f32_kernel(const float* __restrict__ phi, const float* __restrict__ cs,
+                    const float* __restrict__ cl, long long n, DiagConsts C, float* __restrict__ po,
+                    float* __restrict__ co, float* __restrict__ dout, float* __restrict__ clo) {
+    const float a = (float)C.a;
+    const bool cubic = C.interp == 1;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float f = phi[i], s = cs[i], l = cl[i];
+        const float g = f * (1.0f - f);
+        const float h = cubic ? f * f * (3.0f - 2.0f * f) : f * f * f * (f * (6.0f * f - 15.0f) + 10.0f);
+        const float p = h + a * (f - 0.5f) * g * g;
+        float dh, dl;
+        two_sum(s, -l, dh, dl);
+        const float prod = p * dh;
+        const float small = fmaf(p, dl, fmaf(p, dh, -prod));
+        float hi, e;
+        two_sum(l, prod, hi, e);
+        const float lo = e + small;
+        const float c = hi + lo;
+        po[i] = f;
+        co[i] = c;
+        clo[i] = lo - (c - hi);
+        dout[i] = dh;
+    }
+}
+
+// FP32 state: total of c = c_hi + c_lo.  Each thread accumulates its cells as
+// a renormalised float pair (TwoSum), so the FP32 pipes do the work; the
+// per-thread totals then enter the FP64 block reduction.  Deterministic: the
+// cells of a thread and the reduction order are fixed.
+__global__ void __launch_bounds__(DIAG_THREADS)
+solute_f32_kernel(const float* __restrict__ c, const float* __restrict__ clo, long long n,
+                  double* __restrict__ part) {
+    float ah = 0.0f, al = 0.0f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n4 = n / 4;
+    const float4* c4 = reinterpret_cast<const float4*>(c);
+    const float4* l4 = reinterpret_cast<const float4*>(clo);
+    auto add = [&](float x, float y) {
+        float s, e;
+        two_sum(ah, x, s, e);
+        const float t = al + (e + y);
+        ah = s + t;
+        al = t - (ah - s);
+    };
+    for (long long i = t0; i < n4; i += stride) {
+        const float4 x = c4[i], y = l4[i];
+        add(x.x, y.x);
+        add(x.y, y.y);
+        add(x.z, y.z);
+        add(x.w, y.w);
+    }
+    for (long long i = 4 * n4 + t0; i < n; i += stride) add(c[i], clo[i]);
+    double v = (double)ah + (double)al, unused = 0.0;
+    block_reduce2<false>(v, unused);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = 0.0;
+        part[gridDim.x + blockIdx.x] = v;
+    }
+}
+
 template <typename T>
 __global__ void from_state_kernel(StateView<T> S, long long n, DiagConsts C, T* phi, T* cs, T* cl) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -262,7 +337,8 @@ cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t 
         else energy_solute_kernel<double, false><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
     } else {
         if (with_energy) energy_solute_kernel<float, true><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
-        else energy_solute_kernel<float, false><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
+        else solute_f32_kernel<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+            (const float*)f.c, (const float*)f.clo, P.cells(), scratch);
     }
     finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, C.dV, out);
     return cudaGetLastError();
@@ -308,7 +384,7 @@ cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* c
             (const double*)phi, (const double*)cs, (const double*)cl, n, C, (double*)out.phi,
             (double*)out.c, (double*)out.d, nullptr);
     else
-        to_state_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+        to_state_f32_kernel<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
             (const float*)phi, (const float*)cs, (const float*)cl, n, C, (float*)out.phi,
             (float*)out.c, (float*)out.d, (float*)out.clo);
     return cudaGetLastError();

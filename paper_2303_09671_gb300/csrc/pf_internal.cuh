@@ -25,7 +25,33 @@ struct Consts {
     // frozen temperature theta(x,t) = theta0 - G_theta * x_cell, with
     // theta0 = theta_ref + G_theta (x0 + v_pull t - shifts dx) folded on the host
     T G_theta;
+    // h(phi) = phi^2 (h2 + phi (h3 + phi (h4 + phi h5))), h'(phi) = phi (dh1 +
+    // phi (dh2 + phi (dh3 + phi dh4))) and M_i = Mi_c c_i + Mi_0, filled by
+    // set_coefficients() from interp and mobility, so the kernels need no branch
+    T h2, h3, h4, h5, dh1, dh2, dh3, dh4;
+    T Ms_c, Ms_0, Ml_c, Ml_0;
 };
+
+// quintic h = 10 phi^3 - 15 phi^4 + 6 phi^5, cubic h = 3 phi^2 - 2 phi^3
+// (the two choices of Sec. "Choice of interpolation functions"), and the
+// mobility M_i = D_i c_i or the constant D_i
+template <typename T>
+__host__ __device__ inline void set_coefficients(Consts<T>& C) {
+    const bool cubic = C.interp == 1;
+    C.h2 = T(cubic ? 3 : 0);
+    C.h3 = T(cubic ? -2 : 10);
+    C.h4 = T(cubic ? 0 : -15);
+    C.h5 = T(cubic ? 0 : 6);
+    C.dh1 = T(cubic ? 6 : 0);
+    C.dh2 = T(cubic ? -6 : 30);
+    C.dh3 = T(cubic ? 0 : -60);
+    C.dh4 = T(cubic ? 0 : 30);
+    const bool cmob = C.mobility == 1;
+    C.Ms_c = cmob ? T(0) : C.D_s;
+    C.Ms_0 = cmob ? C.D_s : T(0);
+    C.Ml_c = cmob ? T(0) : C.D_l;
+    C.Ml_0 = cmob ? C.D_l : T(0);
+}
 
 // Per-launch time data.
 template <typename T>
@@ -59,26 +85,25 @@ __device__ __forceinline__ double flog(double x) { return log(x); }
 // h(phi), p(phi) = h + a (phi - 1/2) phi^2 (1-phi)^2 (Eq. interpolation2), p'
 template <typename T>
 __device__ __forceinline__ T p_of(const Consts<T>& C, T f) {
-    T g = f * (T(1) - f);
-    T h = (C.interp == 1) ? f * f * (T(3) - T(2) * f)
-                          : f * f * f * (T(6) * f * f - T(15) * f + T(10));
+    const T g = f * (T(1) - f);
+    const T h = f * f * (C.h2 + f * (C.h3 + f * (C.h4 + f * C.h5)));
     return h + C.a * (f - T(0.5)) * g * g;
 }
 template <typename T>
 __device__ __forceinline__ T dp_of(const Consts<T>& C, T f) {
-    T g = f * (T(1) - f);
-    T dh = (C.interp == 1) ? T(6) * g : T(30) * g * g;
-    T w = g * g;
-    T dw = T(2) * g * (T(1) - T(2) * f);
+    const T g = f * (T(1) - f);
+    const T dh = f * (C.dh1 + f * (C.dh2 + f * (C.dh3 + f * C.dh4)));
+    const T w = g * g;
+    const T dw = T(2) * g * (T(1) - T(2) * f);
     return dh + C.a * (w + (f - T(0.5)) * dw);
 }
 template <typename T>
 __device__ __forceinline__ T Ms_of(const Consts<T>& C, T cs) {
-    return C.mobility == 1 ? C.D_s : C.D_s * cs;
+    return C.Ms_c * cs + C.Ms_0;
 }
 template <typename T>
 __device__ __forceinline__ T Ml_of(const Consts<T>& C, T cl) {
-    return C.mobility == 1 ? C.D_l : C.D_l * cl;
+    return C.Ml_c * cl + C.Ml_0;
 }
 
 }  // namespace pf

@@ -54,8 +54,8 @@ struct Tile {
 // the two cells' centred differences; phi, c_s, c_l, d and phidot at the face
 // are the means of the two cells; p, Mbar, q_n and the weights are evaluated
 // at the face phi.
-template <typename T, int TX, int TY, int MINB>
-cudaError_t launch_step3d_tile(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K);
+template <typename T>
+cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K);
 
 template <typename T, int DIM>
 __device__ __forceinline__ void face_flux(const Consts<T>& C, int axis,
@@ -492,6 +492,7 @@ static Consts<T> make_consts(const HostProblem& P) {
     C.delta2 = T(P.delta * P.delta);
     C.dt = T(P.dt);
     C.G_theta = T(P.G_theta);
+    set_coefficients(C);
     return C;
 }
 
@@ -511,8 +512,7 @@ static cudaError_t launch_T(const StepLaunch& a) {
     if (P.dim == 1) return launch_tile<T, 1, 128, 1>(a, C, K);
     if (P.dim == 2) return launch_tile<T, 2, 32, 8>(a, C, K);
     if (a.use_generic3d) return launch_tile<T, 3, 32, 8>(a, C, K);
-    if constexpr (sizeof(T) == 4) return launch_step3d_tile<T, 32, 8, 4>(a, C, K);
-    else return launch_step3d_tile<T, 32, 8, 2>(a, C, K);
+    return launch_step3d<T>(a, C, K);
 }
 
 cudaError_t launch_step(const StepLaunch& a) {

@@ -4,485 +4,752 @@
 // cs_nonvar / cl_nonvar at faces, Eq. phasefield_nonvar at cells with the
 // re-derived driving force, conservative (c, d) update, forward Euler), laid
 // out for throughput on one GB300:
-//   * one CTA = a TX x TY tile of columns marching along z over a chunk of
-//     planes; the grid has several chunks per column so that every SM holds
-//     four CTAs;
-//   * per z-plane, the halo-2 tile of each plane is loaded once and turned
-//     into packed records {phi, Y, mu_s, mu_l} (16 B in FP32) and {c_s, c_l},
-//     kept in shared-memory rings (4 planes of records, 3 of the rest; about
-//     51 KB per CTA in FP32, so that four CTAs share an SM);
-//   * centred gradients are not stored: a face builds its transverse
-//     components from the packed records of its two cells' neighbours, so one
-//     vector load serves all four fields;
-//   * x, y and z faces of a plane are computed in one balanced loop, each face
-//     once, and stored as (F_c, F_d) pairs;
+//   * a CTA owns a TX x TY tile of columns (TY even) and marches along z over a
+//     chunk of planes; thread (tx, ty) owns the two cells (x, y) and (x, y+1),
+//     y = y0 + 2 ty, and evaluates everything for both at once as a two-lane
+//     vector.  In FP32 the lanes are the packed .f32x2 add/mul/fma of sm_100
+//     class GPUs, which do two FP32 operations per issue slot;
+//   * shared memory holds the halo-2 tile of each plane as two-lane records
+//     {phi, Y}, {mu_s, mu_l}, {c_s, c_l} and phi (rings of 4, 4, 3 and 3
+//     planes), the phase-field rate on the halo-1 ring (2 planes) and the
+//     fluxes through the x faces and the upper y face of every cell pair;
+//   * every thread evaluates the x+1/2, y+1/2 and z+1/2 faces of its own two
+//     cells, so the neighbour records the three faces share are read once;
+//     the faces on the tile's low x and low y edges are evaluated by one more
+//     warp each;
+//   * a y shift by one cell moves data between the lanes of neighbouring
+//     records; those values are assembled lane by lane, everything else is
+//     two-lane arithmetic;
+//   * differences are kept in grid units (not divided by dx) and the stored
+//     rate is dx^2 dphi/dt, so that F_c, F_d below are dx times the fluxes of
+//     the model and the update is c += dt/dx^2 sum(F+ - F-);
 //   * FP32 reciprocals use the hardware approximation (a few ulp), FP64 is
 //     exact IEEE.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include "pf_internal.cuh"
 #include "pf_kernels.h"
 
 namespace pf {
 
+// ---------------------------------------------------------------- two lanes
 template <typename T>
-struct alignas(4 * sizeof(T)) V4 {
-    T x, y, z, w;   // phi, Y, mu_s, mu_l
+struct Lanes;
+template <>
+struct Lanes<float> {
+    using V = float2;
 };
-template <typename T>
-struct alignas(2 * sizeof(T)) V2 {
-    T x, y;
+template <>
+struct Lanes<double> {
+    using V = double2;
 };
 
-__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+    unsigned long long ra, rb, rr;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(ra), "l"(rb));
+    float2 r;
+    memcpy(&r, &rr, 8);
+    return r;
+}
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
+__device__ __forceinline__ float2 vlog(float2 a) { return make_float2(logf(a.x), logf(a.y)); }
+__device__ __forceinline__ float2 vpair(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vrcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+__device__ __forceinline__ double2 vlog(double2 a) { return make_double2(log(a.x), log(a.y)); }
+__device__ __forceinline__ double2 vpair(double a, double b) { return make_double2(a, b); }
+
+// two fields of a cell pair: one 16-byte shared-memory access in FP32
+template <typename V>
+struct alignas(2 * sizeof(V)) Q2 {
+    V a, b;
+};
+
+// Parameters, each broadcast to both lanes (so that two-lane instructions
+// can take them as operands), in grid units.
+template <typename V>
+struct PairConsts {
+    V one, two, half, sixteenth, sixteenth_neg, third, sixth, four, six;
+    V h2, h3, h4, h5, dh1, dh2, dh3, dh4, a_int;
+    V Ms_c, Ms_0, Ml_c, Ml_0, b, A, one_m_A, half_one_m_A, one_m_ke, log_ke;
+    V sigma, H, dx2, inv_Mphi, K_anti, delta2_dx2, delta2_4dx2, dt_dx2;
+};
+
+// Grid, boundaries, frozen temperature and the Dirichlet ghost state.
+template <typename T>
+struct GridConsts {
+    int n[3], bc_lo[3], bc_hi[3];
+    T dx, theta0, G_theta;
+    T dir_phi, dir_c, dir_d;   // ghost phi and its c = p c_s + (1-p) c_l, d = c_s - c_l
+};
 
 template <typename T, int TX, int TY>
-struct Tile3 {
-    static constexpr int NT = TX * TY;
-    static constexpr int HX = TX + 4, HY = TY + 4, HP = HX * HY;   // halo-2 plane
-    static constexpr int RX = TX + 2, RY = TY + 2, RP = RX * RY;   // ring-1 plane
-    static constexpr int NS = 4;   // slots of packed records (planes z-1 .. z+2)
-    static constexpr int N3 = 3;   // slots of {c_s, c_l} and phi (planes z .. z+2)
-    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NFZ = TX * TY;
-    static constexpr int NF = NFX + NFY + NFZ;
-    static constexpr size_t OFF_G4 = 0;
-    static constexpr size_t OFF_C2 = OFF_G4 + sizeof(V4<T>) * NS * HP;
-    static constexpr size_t OFF_PH = OFF_C2 + sizeof(V2<T>) * N3 * HP;
-    static constexpr size_t OFF_PD = OFF_PH + sizeof(T) * N3 * HP;
-    static constexpr size_t OFF_FX = OFF_PD + sizeof(T) * 2 * RP;
-    static constexpr size_t OFF_FY = OFF_FX + sizeof(V2<T>) * NFX;
-    static constexpr size_t OFF_FZ = OFF_FY + sizeof(V2<T>) * NFY;
-    static constexpr size_t BYTES = OFF_FZ + sizeof(V2<T>) * NFZ;
+struct PTile {
+    static_assert(TY % 2 == 0, "cells are paired along y");
+    using V = typename Lanes<T>::V;
+    using Q = Q2<V>;
+    static constexpr int TYP = TY / 2;                  // pair rows
+    static constexpr int NT = TX * TYP;                 // threads
+    static constexpr int HX = TX + 4, HYP = TYP + 2;    // halo-2 plane in pairs
+    static constexpr int HP = HX * HYP;
+    static constexpr int RX = TX + 2, RP = RX * HYP;    // halo-1 ring (all pair rows)
+    static constexpr int JH = (HP + NT - 1) / NT;
+    static constexpr int JR = (RP + NT - 1) / NT;
+    static constexpr size_t OFF_A = 0;                                   // {phi, Y}, 4 planes
+    static constexpr size_t OFF_B = OFF_A + sizeof(Q) * 4 * HP;          // {mu_s, mu_l}, 4 planes
+    static constexpr size_t OFF_C = OFF_B + sizeof(Q) * 4 * HP;          // {c_s, c_l}, 3 planes
+    static constexpr size_t OFF_P = OFF_C + sizeof(Q) * 3 * HP;          // phi, 3 planes
+    static constexpr size_t OFF_D = OFF_P + sizeof(V) * 3 * HP;          // dx^2 phidot, 2 planes
+    static constexpr size_t OFF_FX = OFF_D + sizeof(V) * 2 * RP;         // x faces {F_c, F_d}
+    static constexpr size_t OFF_FY = OFF_FX + sizeof(Q) * TYP * (TX + 1);   // upper y face
+    static constexpr size_t OFF_R = OFF_FY + 2 * sizeof(T) * (TYP + 1) * TX;   // next plane: phi, c, d
+    static constexpr size_t OFF_O = OFF_R + sizeof(V) * 3 * HP;               // own c, d, c_lo
+    static constexpr size_t BYTES = OFF_O + sizeof(V) * 3 * NT;
+    static constexpr int NB = RP - NT;   // ring cells besides the threads' own pairs
+    static_assert(NB == 2 * RX + 2 * TYP && NB <= NT, "ring = own pairs + border");
 };
 
-// face fluxes from the face state; nrm = normal differences (R - L) of
-// {phi, Y, mu_s, mu_l} times 1/dx, t1, t2 = the two transverse components.
-// With T_i = M_i [d_a mu_i (|g_t|^2 + delta^2) - g_a (g_t . grad_t mu_i)] (the
-// tangential fluxes times 1/r) and w_s + w_l = 1, p w_s - (1-p) w_l = a(phi):
-//   F_c = r [q g_a (g . grad Y) + p T_s + (1-p) T_l + (1-A) d phidot g_a a(phi)]
-//   F_d = r [T_s - T_l + (1-A) d phidot g_a]
+// asynchronous global -> shared copies (cp.async, completion awaited per thread)
 template <typename T>
-__device__ __forceinline__ V2<T> face3(const Consts<T>& C, T phiL, T phiR, V2<T> cL, V2<T> cR,
-                                       T pdL, T pdR, V4<T> nrm, V4<T> t1, V4<T> t2) {
-    const T f = T(0.5) * (phiL + phiR);
-    const T cs = T(0.5) * (cL.x + cR.x);
-    const T cl = T(0.5) * (cL.y + cR.y);
-    const T d = cs - cl;
-    const T pdot = T(0.5) * (pdL + pdR);
-    const T p = p_of(C, f);
-    const T omp = T(1) - p;
-    const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
-    const T bMl = C.b * Ml;
-    const T iMbar = frcp(Ms * omp + bMl * p);
-    const T gt2d = t1.x * t1.x + t2.x * t2.x + C.delta2;
-    const T ga = nrm.x;
-    const T r = frcp(ga * ga + gt2d);
-    const T dY = ga * nrm.y + t1.x * t1.y + t2.x * t2.y;
-    const T Ts = Ms * (nrm.z * gt2d - ga * (t1.x * t1.z + t2.x * t2.z));
-    const T Tl = Ml * (nrm.w * gt2d - ga * (t1.x * t1.w + t2.x * t2.w));
-    const T at = C.one_m_A * d * pdot * ga;
-    const T q = Ms * Ml * (C.b * p + omp) * iMbar;
-    const T afn = (Ms - bMl) * p * omp * iMbar;
-    V2<T> out;
-    out.x = r * (q * ga * dY + p * Ts + omp * Tl + at * afn);   // F_c
-    out.y = r * (Ts - Tl + at);                                  // F_d
-    return out;
+__device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
 }
-
-template <typename T>
-__device__ __forceinline__ V4<T> sub4(V4<T> a, V4<T> b) {
-    return V4<T>{a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w};
-}
-template <typename T>
-__device__ __forceinline__ V4<T> add4(V4<T> a, V4<T> b) {
-    return V4<T>{a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
-}
-template <typename T>
-__device__ __forceinline__ V4<T> scale4(V4<T> a, T s) {
-    return V4<T>{a.x * s, a.y * s, a.z * s, a.w * s};
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int slot3(int z) { return ((z % 3) + 3) % 3; }
 
-// Per-thread work lists, fixed for the whole z-march: each thread owns up to
-// JH halo cells (plane loads), JR ring cells (phase-field rates) and JF faces.
-template <int TX, int TY>
-struct Work3 {
-    static constexpr int NT = TX * TY;
-    static constexpr int HX = TX + 4, HP = (TX + 4) * (TY + 4);
-    static constexpr int RX = TX + 2, RP = (TX + 2) * (TY + 2);
-    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NFZ = TX * TY;
-    static constexpr int NF = NFX + NFY + NFZ;
-    static constexpr int JH = (HP + NT - 1) / NT;
-    static constexpr int JR = (RP + NT - 1) / NT;
-    static constexpr int JF = (NF + NT - 1) / NT;
-};
-
-// face descriptor packed in 32 bits: bits 0-11 left-cell halo index, 12-23
-// left-cell ring index, 24-25 axis (0 x, 1 y, 2 z, 3 none), 26 no-flux face
-__device__ __forceinline__ unsigned pack_face(int h, int r, int axis, bool nf) {
-    return (unsigned)h | ((unsigned)r << 12) | ((unsigned)axis << 24) | ((unsigned)nf << 26);
+// p(phi) of Eq. interpolation2 and its derivative, two lanes
+template <typename V>
+__device__ __forceinline__ V vp_of(const PairConsts<V>& K, V f) {
+    const V g = vmul(f, vsub(K.one, f));
+    const V h = vmul(vmul(f, f), vfma(f, vfma(f, vfma(f, K.h5, K.h4), K.h3), K.h2));
+    return vfma(vmul(K.a_int, vsub(f, K.half)), vmul(g, g), h);
+}
+template <typename V>
+__device__ __forceinline__ V vdp_of(const PairConsts<V>& K, V f) {
+    const V g = vmul(f, vsub(K.one, f));
+    const V dh = vmul(f, vfma(f, vfma(f, vfma(f, K.dh4, K.dh3), K.dh2), K.dh1));
+    // d/dphi [g^2 (phi - 1/2)] = g^2 + 2 g (1 - 2 phi)(phi - 1/2) = g^2 - 4 g (phi - 1/2)^2
+    const V s = vsub(f, K.half);
+    const V w = vmul(g, vsub(g, vmul(K.four, vmul(s, s))));
+    return vfma(K.a_int, w, dh);
 }
 
-template <typename T, int TX, int TY, int MINB>
-__global__ void __launch_bounds__(TX * TY, MINB)
-step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in,
-              const T* __restrict__ d_in, const T* __restrict__ clo_in,
-              T* __restrict__ phi_out, T* __restrict__ c_out, T* __restrict__ d_out,
-              T* __restrict__ clo_out, Consts<T> C, Clock<T> K, int zchunk) {
-    using L = Tile3<T, TX, TY>;
-    using W = Work3<TX, TY>;
-    static_assert(L::HP < 4096 && L::RP < 4096, "tile too large for the packed descriptors");
+// Fluxes through a face (dx times F_c, F_d of the model) from the face state:
+// f, c_s, c_l = face means; pds = sum of the two cells' dx^2 phidot; n = the
+// normal differences R - L of {phi, Y, mu_s, mu_l}; t1, t2 = the transverse
+// sums of four centred differences (4 dx times the face's transverse
+// gradient).  With T_i = M_i [n_i (|t|^2/16 + delta^2 dx^2) - n_phi (t.t_i)/16]
+// and w_s + w_l = 1, p w_s - (1-p) w_l = a(phi) (Eq. shape_function):
+//   F_c = r [q n_phi (n_phi n_Y + t.t_Y/16) + p T_s + (1-p) T_l + at a(phi)]
+//   F_d = r [T_s - T_l + at],  at = (1-A) d phidot dx^2 n_phi,
+//   r = 1/(n_phi^2 + |t|^2/16 + delta^2 dx^2)
+template <typename V>
+__device__ __forceinline__ void face_flux(const PairConsts<V>& K, V f, V cs, V cl, V pds, const V n[4],
+                                          const V t1[4], const V t2[4], V& Fc, V& Fd) {
+    const V d = vsub(cs, cl);
+    const V p = vp_of(K, f);
+    const V omp = vsub(K.one, p);
+    const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
+    const V bMl = vmul(K.b, Ml);
+    const V iMbar = vrcp(vfma(bMl, p, vmul(Ms, omp)));
+    const V tt = vfma(t1[0], t1[0], vmul(t2[0], t2[0]));
+    const V gt2d = vfma(tt, K.sixteenth, K.delta2_dx2);
+    const V r = vrcp(vfma(n[0], n[0], gt2d));
+    const V m = vmul(n[0], K.sixteenth_neg);          // -n_phi / 16
+    const V dY = vfma(vfma(t1[0], t1[1], vmul(t2[0], t2[1])), K.sixteenth, vmul(n[0], n[1]));
+    const V Ts = vmul(Ms, vfma(m, vfma(t1[0], t1[2], vmul(t2[0], t2[2])), vmul(n[2], gt2d)));
+    const V Tl = vmul(Ml, vfma(m, vfma(t1[0], t1[3], vmul(t2[0], t2[3])), vmul(n[3], gt2d)));
+    const V at = vmul(vmul(K.half_one_m_A, pds), vmul(d, n[0]));
+    const V pomp = vmul(p, omp);
+    const V q = vmul(vmul(Ms, Ml), vmul(vfma(K.b, p, omp), iMbar));
+    const V afn = vmul(vsub(Ms, bMl), vmul(pomp, iMbar));
+    V acc = vmul(vmul(q, n[0]), dY);
+    acc = vfma(p, Ts, acc);
+    acc = vfma(omp, Tl, acc);
+    acc = vfma(at, afn, acc);
+    Fc = vmul(r, acc);
+    Fd = vmul(r, vadd(vsub(Ts, Tl), at));
+}
+
+// lane-wise zero
+template <typename V>
+__device__ __forceinline__ V vmask(V v, bool zero_lo, bool zero_hi) {
+    if (zero_lo) v.x = 0;
+    if (zero_hi) v.y = 0;
+    return v;
+}
+
+template <typename T, int TX, int TY, bool L19>
+__global__ void __launch_bounds__(TX * (TY / 2), (sizeof(T) == 4 ? 2 : 1))
+step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
+              const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
+              T* __restrict__ d_out, T* __restrict__ clo_out, const PairConsts<typename Lanes<T>::V> K,
+              const GridConsts<T> G, int zchunk) {
+    using L = PTile<T, TX, TY>;
+    using V = typename L::V;
+    using Q = typename L::Q;
+    constexpr int HX = L::HX, HP = L::HP, RX = L::RX, RP = L::RP, NT = L::NT, TYP = L::TYP;
+    static_assert(HP < 4096, "tile too large for the packed ring descriptors");
+    static_assert(NT >= 32 + TX && TYP <= 32, "edge faces need warps 0 and 1");
     extern __shared__ __align__(16) unsigned char smem[];
-    V4<T>* sG4 = reinterpret_cast<V4<T>*>(smem + L::OFF_G4);
-    V2<T>* sC2 = reinterpret_cast<V2<T>*>(smem + L::OFF_C2);
-    T* sPh = reinterpret_cast<T*>(smem + L::OFF_PH);
-    T* sPd = reinterpret_cast<T*>(smem + L::OFF_PD);
-    V2<T>* sFx = reinterpret_cast<V2<T>*>(smem + L::OFF_FX);
-    V2<T>* sFy = reinterpret_cast<V2<T>*>(smem + L::OFF_FY);
-    V2<T>* sFz = reinterpret_cast<V2<T>*>(smem + L::OFF_FZ);
+    Q* sA = reinterpret_cast<Q*>(smem + L::OFF_A);
+    Q* sB = reinterpret_cast<Q*>(smem + L::OFF_B);
+    Q* sC = reinterpret_cast<Q*>(smem + L::OFF_C);
+    V* sP = reinterpret_cast<V*>(smem + L::OFF_P);
+    V* sD = reinterpret_cast<V*>(smem + L::OFF_D);
+    Q* sFx = reinterpret_cast<Q*>(smem + L::OFF_FX);
+    T* sFy = reinterpret_cast<T*>(smem + L::OFF_FY);
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int nx = C.n[0], ny = C.n[1], nz = C.n[2];
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
     const long long sz = (long long)nx * ny;
-    const T q_inv_dx = T(0.25) * C.inv_dx;      // mean of two centred differences (f+ - f-)/(2 dx)
 
-    // ---- work lists (independent of z)
-    int hoff[W::JH];          // in-plane global offset of each owned halo cell, -1: Dirichlet ghost
+    // ---- work lists, fixed for the whole z-march
+    int hoff[L::JH][2];   // in-plane offsets of the two rows of each loaded pair cell, -1: ghost
 #pragma unroll
-    for (int j = 0; j < W::JH; ++j) {
-        const int h = tid + j * W::NT;
-        hoff[j] = -1;
-        if (h < L::HP) {
-            const int mx = map_coord(x0 - 2 + h % L::HX, nx, C.bc_lo[0], C.bc_hi[0]);
-            const int my = map_coord(y0 - 2 + h / L::HX, ny, C.bc_lo[1], C.bc_hi[1]);
-            if (mx >= 0 && my >= 0) hoff[j] = my * nx + mx;
+    for (int j = 0; j < L::JH; ++j) {
+        const int h = tid + j * NT;
+        hoff[j][0] = hoff[j][1] = -1;
+        if (h < HP) {
+            const int mx = map_coord(x0 - 2 + h % HX, nx, G.bc_lo[0], G.bc_hi[0]);
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const int my = map_coord(y0 - 2 + 2 * (h / HX) + l, ny, G.bc_lo[1], G.bc_hi[1]);
+                if (mx >= 0 && my >= 0) hoff[j][l] = my * nx + mx;
+            }
         }
     }
-    int rdesc[W::JR];         // halo index of each owned ring cell | Dirichlet flag << 12
-    T rxc[W::JR];             // x coordinate of its (mapped) centre, for theta
-#pragma unroll
-    for (int j = 0; j < W::JR; ++j) {
-        const int r = tid + j * W::NT;
-        rdesc[j] = 0;
-        rxc[j] = T(0);
-        if (r < L::RP) {
-            const int rx = r % L::RX, ry = r / L::RX;
-            const int gx = x0 - 1 + rx;
-            const int mx = map_coord(gx, nx, C.bc_lo[0], C.bc_hi[0]);
-            const bool dir = mx < 0 || map_coord(y0 - 1 + ry, ny, C.bc_lo[1], C.bc_hi[1]) < 0;
-            rdesc[j] = ((ry + 1) * L::HX + rx + 1) | ((int)dir << 12);
-            rxc[j] = (T((mx < 0) ? gx : mx) + T(0.5)) * C.dx;
-        }
+    // ring cells: every thread its own pair, the last NB threads one border cell.
+    // descriptor = halo index | ghost lanes << 12, 13 | first, last pair row << 14, 15
+    auto ring_desc = [&](int rx, int ry, int& dsc, T& xc) {
+        const int gx = x0 - 1 + rx;
+        const int mx = map_coord(gx, nx, G.bc_lo[0], G.bc_hi[0]);
+        const bool glo = mx < 0 || map_coord(y0 - 2 + 2 * ry, ny, G.bc_lo[1], G.bc_hi[1]) < 0;
+        const bool ghi = mx < 0 || map_coord(y0 - 1 + 2 * ry, ny, G.bc_lo[1], G.bc_hi[1]) < 0;
+        dsc = (ry * HX + rx + 1) | ((int)glo << 12) | ((int)ghi << 13) | ((int)(ry == 0) << 14) |
+              ((int)(ry == L::HYP - 1) << 15);
+        xc = (T((mx < 0) ? gx : mx) + T(0.5)) * G.dx;   // theta at the mirror / wrap image
+    };
+    int own_dsc, bor_dsc = 0, bor_r = -1;
+    T own_xc, bor_xc = T(0);
+    ring_desc(tx + 1, ty + 1, own_dsc, own_xc);
+    constexpr int NB = L::NB;
+    if (tid >= NT - NB) {
+        const int b = tid - (NT - NB);
+        int rx, ry;
+        if (b < RX) { rx = b; ry = 0; }
+        else if (b < 2 * RX) { rx = b - RX; ry = L::HYP - 1; }
+        else if (b < 2 * RX + TYP) { rx = 0; ry = 1 + b - 2 * RX; }
+        else { rx = RX - 1; ry = 1 + b - 2 * RX - TYP; }
+        ring_desc(rx, ry, bor_dsc, bor_xc);
+        bor_r = ry * RX + rx;
     }
-    unsigned fdesc[W::JF];
-#pragma unroll
-    for (int j = 0; j < W::JF; ++j) {
-        const int f = tid + j * W::NT;
-        fdesc[j] = pack_face(0, 0, 3, false);
-        if (f < L::NFX) {
-            const int fx = f % (TX + 1), fy = f / (TX + 1);
-            const int gxl = x0 + fx - 1;
-            const bool nf = (gxl == -1 && C.bc_lo[0] == BC_NOFLUX) || (gxl == nx - 1 && C.bc_hi[0] == BC_NOFLUX);
-            fdesc[j] = pack_face((fy + 2) * L::HX + fx + 1, (fy + 1) * L::RX + fx, 0, nf);
-        } else if (f < L::NFX + L::NFY) {
-            const int e = f - L::NFX;
-            const int fx = e % TX, fy = e / TX;
-            const int gyl = y0 + fy - 1;
-            const bool nf = (gyl == -1 && C.bc_lo[1] == BC_NOFLUX) || (gyl == ny - 1 && C.bc_hi[1] == BC_NOFLUX);
-            fdesc[j] = pack_face((fy + 1) * L::HX + fx + 2, fy * L::RX + fx + 1, 1, nf);
-        } else if (f < L::NF) {
-            const int e = f - L::NFX - L::NFY;
-            const int cx = e % TX, cy = e / TX;
-            fdesc[j] = pack_face((cy + 2) * L::HX + cx + 2, (cy + 1) * L::RX + cx + 1, 2, false);
-        }
-    }
-    const int own_h = (ty + 2) * L::HX + tx + 2;
-    const int own_r = (ty + 1) * L::RX + tx + 1;
-    const bool own_in = (x0 + tx < nx) && (y0 + ty < ny);
-    const long long own_xy = (long long)(y0 + ty) * nx + (x0 + tx);
+    const int own_h = (ty + 1) * HX + tx + 2;
+    const int own_r = (ty + 1) * RX + tx + 1;
+    const int own_x = x0 + tx, own_y = y0 + 2 * ty;
+    const bool in_lo = own_x < nx && own_y < ny;
+    const bool in_hi = own_x < nx && own_y + 1 < ny;
+    const long long own_xy = (long long)own_y * nx + own_x;
+    const bool nf_x = own_x == nx - 1 && G.bc_hi[0] == BC_NOFLUX;
+    const bool nf_ylo = own_y == ny - 1 && G.bc_hi[1] == BC_NOFLUX;
+    const bool nf_yhi = own_y + 1 == ny - 1 && G.bc_hi[1] == BC_NOFLUX;
+    const bool nf_x_edge = x0 == 0 && G.bc_lo[0] == BC_NOFLUX;
+    const bool nf_y_edge = y0 == 0 && G.bc_lo[1] == BC_NOFLUX;
 
-    // ---- A: plane z into the rings, from values fetched by fetch_plane
-    T pf_f[W::JH], pf_c[W::JH], pf_d[W::JH];
+    // ---- A: plane z -> staging (asynchronous copies; ghosts written directly).
+    // The thread that copies a pair cell is the one that converts it.
+    T* sR = reinterpret_cast<T*>(smem + L::OFF_R);   // [field][h][lane]
+    T* sO = reinterpret_cast<T*>(smem + L::OFF_O);   // [field][tid][lane]
     auto fetch_plane = [&](int z) {
-        const int mz = map_coord(z, nz, C.bc_lo[2], C.bc_hi[2]);
+        const int mz = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]);
 #pragma unroll
-        for (int j = 0; j < W::JH; ++j) {
-            pf_f[j] = pf_c[j] = pf_d[j] = T(0);
-            if (mz >= 0 && hoff[j] >= 0) {
-                const long long gi = (long long)mz * sz + hoff[j];
-                pf_f[j] = phi_in[gi];
-                pf_c[j] = c_in[gi];
-                pf_d[j] = d_in[gi];
-            }
-        }
-    };
-    auto store_plane = [&](int z) {
-        const bool dirz = map_coord(z, nz, C.bc_lo[2], C.bc_hi[2]) < 0;
-        V4<T>* g4 = sG4 + (z & 3) * L::HP;
-        V2<T>* c2 = sC2 + slot3(z) * L::HP;
-        T* ph = sPh + slot3(z) * L::HP;
+        for (int j = 0; j < L::JH; ++j) {
+            const int h = tid + j * NT;
+            if ((j + 1) * NT > HP && h >= HP) break;
 #pragma unroll
-        for (int j = 0; j < W::JH; ++j) {
-            const int h = tid + j * W::NT;
-            if (j * W::NT + W::NT > L::HP && h >= L::HP) break;
-            T f, cs, cl, p;
-            if (dirz || hoff[j] < 0) {
-                f = C.dir_phi; cs = C.dir_cs; cl = C.dir_cl;
-                p = p_of(C, f);
-            } else {
-                f = pf_f[j];
-                p = p_of(C, f);
-                cs = pf_c[j] + (T(1) - p) * pf_d[j];
-                cl = pf_c[j] - p * pf_d[j];
-            }
-            const T mus = flog(cs) - C.log_ke;
-            const T mul = flog(cl);
-            g4[h] = V4<T>{f, mul + p * (mus - mul), mus, mul};
-            c2[h] = V2<T>{cs, cl};
-            ph[h] = f;
-        }
-    };
-
-    // ---- B: phase-field rate of plane z on the ring-1 region -> sPd[z & 1]
-    auto rates_plane = [&](int z) {
-        const bool dirz = map_coord(z, nz, C.bc_lo[2], C.bc_hi[2]) < 0;
-        T* pdz = sPd + (z & 1) * L::RP;
-        const V4<T>* G0 = sG4 + (z & 3) * L::HP;
-        const V4<T>* GM = sG4 + ((z - 1) & 3) * L::HP;
-        const V4<T>* GP = sG4 + ((z + 1) & 3) * L::HP;
-        const V2<T>* C0 = sC2 + slot3(z) * L::HP;
-        const T* P0 = sPh + slot3(z) * L::HP;
-        const T* PM = sPh + slot3(z - 1) * L::HP;
-        const T* PP = sPh + slot3(z + 1) * L::HP;
-#pragma unroll
-        for (int j = 0; j < W::JR; ++j) {
-            const int r = tid + j * W::NT;
-            if (j * W::NT + W::NT > L::RP && r >= L::RP) break;
-            const int h = rdesc[j] & 0xfff;
-            T pd = T(0);
-            if (!dirz && !(rdesc[j] >> 12)) {
-                const V4<T> c0 = G0[h];
-                const V4<T> ex = sub4(G0[h + 1], G0[h - 1]);
-                const V4<T> ey = sub4(G0[h + L::HX], G0[h - L::HX]);
-                const V4<T> ez = sub4(GP[h], GM[h]);
-                const V2<T> cc = C0[h];
-                const T fc = c0.x;
-                const T faces = P0[h - 1] + P0[h + 1] + P0[h - L::HX] + P0[h + L::HX] + PM[h] + PP[h];
-                T lap;
-                if (C.lap == 7) {
-                    lap = faces - T(6) * fc;
+            for (int l = 0; l < 2; ++l) {
+                T* dst = sR + 2 * h + l;
+                if (mz >= 0 && hoff[j][l] >= 0) {
+                    const long long gi = (long long)mz * sz + hoff[j][l];
+                    cp_async(dst, phi_in + gi);
+                    cp_async(dst + 2 * HP, c_in + gi);
+                    cp_async(dst + 4 * HP, d_in + gi);
                 } else {
-                    const T edges = P0[h + L::HX + 1] + P0[h + L::HX - 1] + P0[h - L::HX + 1] +
-                                    P0[h - L::HX - 1] + PP[h + 1] + PP[h - 1] + PM[h + 1] + PM[h - 1] +
-                                    PP[h + L::HX] + PP[h - L::HX] + PM[h + L::HX] + PM[h - L::HX];
-                    lap = T(1.0 / 3.0) * faces + T(1.0 / 6.0) * edges - T(4) * fc;
+                    dst[0] = G.dir_phi;
+                    dst[2 * HP] = G.dir_c;
+                    dst[4 * HP] = G.dir_d;
                 }
-                lap *= C.inv_dx2;
-                const T cs = cc.x, cl = cc.y, mus = c0.z, mul = c0.w;
-                const T p = p_of(C, fc), dp = dp_of(C, fc);
-                const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
-                const T bMl = C.b * Ml;
-                const T Msq = Ms * (T(1) - p);
-                const T iMbar = frcp(Msq + bMl * p);
-                const T d = cs - cl;
-                const T s2 = C.inv_2dx * C.inv_2dx;
-                const T g2 = (ex.x * ex.x + ey.x * ey.x + ez.x * ez.x) * s2;
-                const T cross = ((Ms * ex.z - bMl * ex.w) * ex.x + (Ms * ey.z - bMl * ey.w) * ey.x +
-                                 (Ms * ez.z - bMl * ez.w) * ez.x) * s2;
-                const T rr = frcp(g2 + C.delta2);
-                const T pq = p * (T(1) - p);
-                const T Kc = C.inv_Mphi + C.one_m_A * C.one_m_A * d * d * C.b * pq * rr * iMbar *
-                                              frcp(C.b * p + T(1) - p);
-                const T theta = K.theta0 - C.G_theta * rxc[j];
-                const T dmu = mus - mul;
-                // DeltaG = c_s (mu_s - mu_l) - d - (1-k_e) theta - D d (mu_s - mu_l)
-                const T Dd = (Msq * (T(1) - C.A * (T(1) - p)) + C.A * bMl * p * p) * iMbar;
-                const T dG = cs * dmu - d - C.one_m_ke * theta - Dd * d * dmu;
-                const T dfdw = T(2) * fc * (T(1) - fc) * (T(1) - T(2) * fc);
-                const T R = C.sigma * lap - C.H * dfdw - dG * dp + C.one_m_A * d * pq * iMbar * cross * rr;
-                pd = R * frcp(Kc);
             }
-            pdz[r] = pd;
+        }
+    };
+    auto fetch_own = [&](int z) {
+        const long long gi = (long long)z * sz + own_xy;
+        T* dst = sO + 2 * tid;
+        if (in_lo) {
+            cp_async(dst, c_in + gi);
+            cp_async(dst + 2 * NT, d_in + gi);
+            if (clo_in != nullptr) cp_async(dst + 4 * NT, clo_in + gi);
+        }
+        if (in_hi) {
+            cp_async(dst + 1, c_in + gi + nx);
+            cp_async(dst + 1 + 2 * NT, d_in + gi + nx);
+            if (clo_in != nullptr) cp_async(dst + 1 + 4 * NT, clo_in + gi + nx);
+        }
+    };
+    // staged plane z into the rings
+    auto store_plane = [&](int z) {
+        Q* A = sA + (z & 3) * HP;
+        Q* B = sB + (z & 3) * HP;
+        Q* C = sC + slot3(z) * HP;
+        V* P = sP + slot3(z) * HP;
+        const V* R = reinterpret_cast<const V*>(sR);
+#pragma unroll
+        for (int j = 0; j < L::JH; ++j) {
+            const int h = tid + j * NT;
+            if ((j + 1) * NT > HP && h >= HP) break;
+            const V f = R[h], c = R[HP + h], d = R[2 * HP + h];
+            const V p = vp_of(K, f);
+            const V cs = vfma(vsub(K.one, p), d, c);
+            const V cl = vsub(c, vmul(p, d));
+            const V mus = vsub(vlog(cs), K.log_ke);
+            const V mul = vlog(cl);
+            A[h] = Q{f, vfma(p, vsub(mus, mul), mul)};
+            B[h] = Q{mus, mul};
+            C[h] = Q{cs, cl};
+            P[h] = f;
         }
     };
 
-    // ---- C: every face of plane z (x, y in the plane; z between z and z+1)
-    auto faces_plane = [&](int z) {
-        const V4<T>* G0 = sG4 + (z & 3) * L::HP;
-        const V4<T>* GM = sG4 + ((z - 1) & 3) * L::HP;
-        const V4<T>* GP = sG4 + ((z + 1) & 3) * L::HP;
-        const V2<T>* C0 = sC2 + slot3(z) * L::HP;
-        const V2<T>* CP = sC2 + slot3(z + 1) * L::HP;
-        const T* pd0 = sPd + (z & 1) * L::RP;
-        const T* pd1 = sPd + ((z + 1) & 1) * L::RP;
-        const bool znf = (z == -1 && C.bc_lo[2] == BC_NOFLUX) || (z == nz - 1 && C.bc_hi[2] == BC_NOFLUX);
-#pragma unroll
-        for (int j = 0; j < W::JF; ++j) {
-            const int f = tid + j * W::NT;
-            const unsigned dsc = fdesc[j];
-            const int axis = (dsc >> 24) & 3;
-            if (axis == 3) break;
-            const int hL = dsc & 0xfff, rL = (dsc >> 12) & 0xfff;
-            const bool nf = (dsc >> 26) & 1;
-            V2<T> F{T(0), T(0)};
-            if (axis == 0) {
-                if (!nf) {
-                    const int hR = hL + 1;
-                    const V4<T> aL = G0[hL], aR = G0[hR];
-                    const V4<T> ty_ = scale4(add4(sub4(G0[hL + L::HX], G0[hL - L::HX]),
-                                                  sub4(G0[hR + L::HX], G0[hR - L::HX])), q_inv_dx);
-                    const V4<T> tz_ = scale4(add4(sub4(GP[hL], GM[hL]), sub4(GP[hR], GM[hR])), q_inv_dx);
-                    F = face3(C, aL.x, aR.x, C0[hL], C0[hR], pd0[rL], pd0[rL + 1],
-                              scale4(sub4(aR, aL), C.inv_dx), ty_, tz_);
-                }
-                sFx[f] = F;
-            } else if (axis == 1) {
-                if (!nf) {
-                    const int hR = hL + L::HX;
-                    const V4<T> aL = G0[hL], aR = G0[hR];
-                    const V4<T> tx_ = scale4(add4(sub4(G0[hL + 1], G0[hL - 1]), sub4(G0[hR + 1], G0[hR - 1])),
-                                             q_inv_dx);
-                    const V4<T> tz_ = scale4(add4(sub4(GP[hL], GM[hL]), sub4(GP[hR], GM[hR])), q_inv_dx);
-                    F = face3(C, aL.x, aR.x, C0[hL], C0[hR], pd0[rL], pd0[rL + L::RX],
-                              scale4(sub4(aR, aL), C.inv_dx), tx_, tz_);
-                }
-                sFy[f - L::NFX] = F;
+    // ---- B: dx^2 phidot of one ring pair cell of plane z -> sD[z & 1][r]
+    auto rate_cell = [&](int z, int dsc, T xc, int r) {
+        const bool ghost_z = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) < 0;
+        V* D = sD + (z & 1) * RP;
+        const V* P0 = sP + slot3(z) * HP;
+        const V* PM = sP + slot3(z - 1) * HP;
+        const V* PP = sP + slot3(z + 1) * HP;
+        const Q* B0 = sB + (z & 3) * HP;
+        const Q* BM = sB + ((z - 1) & 3) * HP;
+        const Q* BP = sB + ((z + 1) & 3) * HP;
+        const Q* C0 = sC + slot3(z) * HP;
+        const int h = dsc & 0xfff;
+        const int hS = ((dsc >> 14) & 1) ? h : h - HX;   // first pair row: row below unused
+        const int hN = ((dsc >> 15) & 1) ? h : h + HX;   // last pair row: row above unused
+        V pd = vpair(T(0), T(0));
+        if (!ghost_z) {
+            const V f = P0[h];
+            const V fxm = P0[h - 1], fxp = P0[h + 1], fS = P0[hS], fN = P0[hN];
+            const V fzm = PM[h], fzp = PP[h];
+            const V XP = vadd(fxm, fxp), ZP = vadd(fzm, fzp);
+            const V YF = vpair(fS.y + f.y, f.x + fN.x);
+            V lap;
+            if (L19) {
+                const V XS = vadd(P0[hS - 1], P0[hS + 1]), XN = vadd(P0[hN - 1], P0[hN + 1]);
+                const V ZS = vadd(PM[hS], PP[hS]), ZN = vadd(PM[hN], PP[hN]);
+                const V EXY = vpair(XS.y + XP.y, XP.x + XN.x);
+                const V EZY = vpair(ZS.y + ZP.y, ZP.x + ZN.x);
+                const V EXZ = vadd(vadd(PM[h - 1], PM[h + 1]), vadd(PP[h - 1], PP[h + 1]));
+                lap = vsub(vfma(K.third, vadd(vadd(XP, ZP), YF), vmul(K.sixth, vadd(vadd(EXY, EZY), EXZ))),
+                           vmul(K.four, f));
             } else {
-                if (!znf) {
-                    const V4<T> aL = G0[hL], aR = GP[hL];
-                    const V4<T> tx_ = scale4(add4(sub4(G0[hL + 1], G0[hL - 1]), sub4(GP[hL + 1], GP[hL - 1])),
-                                             q_inv_dx);
-                    const V4<T> ty_ = scale4(add4(sub4(G0[hL + L::HX], G0[hL - L::HX]),
-                                                  sub4(GP[hL + L::HX], GP[hL - L::HX])), q_inv_dx);
-                    F = face3(C, aL.x, aR.x, C0[hL], CP[hL], pd0[rL], pd1[rL],
-                              scale4(sub4(aR, aL), C.inv_dx), tx_, ty_);
-                }
-                sFz[f - L::NFX - L::NFY] = F;   // face (z, z+1)
+                lap = vsub(vadd(vadd(XP, ZP), YF), vmul(K.six, f));
             }
+            const Q cc = C0[h], bc = B0[h];
+            const Q bxm = B0[h - 1], bxp = B0[h + 1], bS = B0[hS], bN = B0[hN], bzm = BM[h], bzp = BP[h];
+            // centred differences (times 2 dx) of phi, mu_s, mu_l
+            const V gx = vsub(fxp, fxm), gy = vpair(f.y - fS.y, fN.x - f.x), gz = vsub(fzp, fzm);
+            const V sx = vsub(bxp.a, bxm.a), sy = vpair(bc.a.y - bS.a.y, bN.a.x - bc.a.x), sz_ = vsub(bzp.a, bzm.a);
+            const V lx = vsub(bxp.b, bxm.b), ly = vpair(bc.b.y - bS.b.y, bN.b.x - bc.b.x), lz = vsub(bzp.b, bzm.b);
+            const V cs = cc.a, cl = cc.b, mus = bc.a, mul = bc.b;
+            const V p = vp_of(K, f), dp = vdp_of(K, f);
+            const V omp = vsub(K.one, p);
+            const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
+            const V bMl = vmul(K.b, Ml);
+            const V Msq = vmul(Ms, omp);
+            const V iMbar = vrcp(vfma(bMl, p, Msq));
+            const V d = vsub(cs, cl);
+            const V g2 = vfma(gx, gx, vfma(gy, gy, vmul(gz, gz)));
+            const V ds = vfma(sx, gx, vfma(sy, gy, vmul(sz_, gz)));
+            const V dl = vfma(lx, gx, vfma(ly, gy, vmul(lz, gz)));
+            const V cross = vsub(vmul(Ms, ds), vmul(bMl, dl));     // (M_s grad mu_s - b M_l grad mu_l).grad phi
+            const V rr = vrcp(vadd(g2, K.delta2_4dx2));
+            const V pq = vmul(p, omp);
+            const V Kc = vfma(K.K_anti, vmul(vmul(vmul(d, d), vmul(pq, rr)), vmul(iMbar, vrcp(vfma(K.b, p, omp)))),
+                              K.inv_Mphi);
+            const T th_s = G.theta0 - G.G_theta * xc;
+            const V theta = vpair(th_s, th_s);
+            const V dmu = vsub(mus, mul);
+            // D = [M_s (1-p)(1 - A(1-p)) + A b M_l p^2] / Mbar
+            const V Dd = vmul(vfma(Msq, vsub(K.one, vmul(K.A, omp)), vmul(vmul(K.A, bMl), vmul(p, p))), iMbar);
+            // DeltaG = c_s (mu_s - mu_l) - d - (1-k_e) theta - D d (mu_s - mu_l)
+            const V dG = vsub(vsub(vmul(cs, dmu), d), vfma(K.one_m_ke, theta, vmul(vmul(Dd, d), dmu)));
+            const V g = vmul(f, vsub(K.one, f));
+            const V dfdw = vmul(g, vsub(K.two, vmul(K.four, f)));
+            const V anti = vmul(vmul(vmul(K.one_m_A, d), vmul(pq, iMbar)), vmul(cross, rr));
+            const V R = vfma(K.sigma, lap, vmul(K.dx2, vsub(anti, vfma(K.H, dfdw, vmul(dG, dp)))));
+            pd = vmask(vmul(R, vrcp(Kc)), (dsc >> 12) & 1, (dsc >> 13) & 1);
         }
+        D[r] = pd;
+    };
+    auto rates_plane = [&](int z) {
+        rate_cell(z, own_dsc, own_xc, own_r);
+        if (bor_r >= 0) rate_cell(z, bor_dsc, bor_xc, bor_r);
+    };
+
+    // ---- C: faces.  Components 0..3 = phi, Y, mu_s, mu_l = (A.a, A.b, B.a, B.b).
+    // x face between halo cells hL and hL + 1 (ring index rL of hL) on plane z
+    auto xface = [&](int z, int hL, int rL, V& Fc, V& Fd) {
+        const Q* A0 = sA + (z & 3) * HP;
+        const Q* AM = sA + ((z - 1) & 3) * HP;
+        const Q* AP = sA + ((z + 1) & 3) * HP;
+        const Q* B0 = sB + (z & 3) * HP;
+        const Q* BM = sB + ((z - 1) & 3) * HP;
+        const Q* BP = sB + ((z + 1) & 3) * HP;
+        const Q* C0 = sC + slot3(z) * HP;
+        const V* D0 = sD + (z & 1) * RP;
+        const int hR = hL + 1;
+        const Q aL = A0[hL], aR = A0[hR], bL = B0[hL], bR = B0[hR];
+        V n[4] = {vsub(aR.a, aL.a), vsub(aR.b, aL.b), vsub(bR.a, bL.a), vsub(bR.b, bL.b)};
+        // y: the rows of a pair are its two lanes
+        const Q aS = A0[hL - HX], aS1 = A0[hR - HX], aN = A0[hL + HX], aN1 = A0[hR + HX];
+        const Q bS = B0[hL - HX], bS1 = B0[hR - HX], bN = B0[hL + HX], bN1 = B0[hR + HX];
+        V SP[4] = {vadd(aL.a, aR.a), vadd(aL.b, aR.b), vadd(bL.a, bR.a), vadd(bL.b, bR.b)};
+        V SS[4] = {vadd(aS.a, aS1.a), vadd(aS.b, aS1.b), vadd(bS.a, bS1.a), vadd(bS.b, bS1.b)};
+        V SN[4] = {vadd(aN.a, aN1.a), vadd(aN.b, aN1.b), vadd(bN.a, bN1.a), vadd(bN.b, bN1.b)};
+        V t1[4], t2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t1[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
+        const Q aPL = AP[hL], aPR = AP[hR], aML = AM[hL], aMR = AM[hR];
+        const Q bPL = BP[hL], bPR = BP[hR], bML = BM[hL], bMR = BM[hR];
+        t2[0] = vsub(vadd(aPL.a, aPR.a), vadd(aML.a, aMR.a));
+        t2[1] = vsub(vadd(aPL.b, aPR.b), vadd(aML.b, aMR.b));
+        t2[2] = vsub(vadd(bPL.a, bPR.a), vadd(bML.a, bMR.a));
+        t2[3] = vsub(vadd(bPL.b, bPR.b), vadd(bML.b, bMR.b));
+        const Q cL = C0[hL], cR = C0[hR];
+        face_flux(K, vmul(K.half, SP[0]), vmul(K.half, vadd(cL.a, cR.a)), vmul(K.half, vadd(cL.b, cR.b)),
+                  vadd(D0[rL], D0[rL + 1]), n, t1, t2, Fc, Fd);
+    };
+    // y faces above the two rows of the pair at hL: lanes (y+1/2, y+3/2)
+    auto yface = [&](int z, int hL, int rL, V& Fc, V& Fd) {
+        const Q* A0 = sA + (z & 3) * HP;
+        const Q* AM = sA + ((z - 1) & 3) * HP;
+        const Q* AP = sA + ((z + 1) & 3) * HP;
+        const Q* B0 = sB + (z & 3) * HP;
+        const Q* BM = sB + ((z - 1) & 3) * HP;
+        const Q* BP = sB + ((z + 1) & 3) * HP;
+        const Q* C0 = sC + slot3(z) * HP;
+        const V* D0 = sD + (z & 1) * RP;
+        const int hN = hL + HX;
+        const Q aP = A0[hL], aN = A0[hN], bP = B0[hL], bN = B0[hN];
+        const V cP[4] = {aP.a, aP.b, bP.a, bP.b};
+        const V cN[4] = {aN.a, aN.b, bN.a, bN.b};
+        V n[4], t1[4], t2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) n[k] = vpair(cP[k].y - cP[k].x, cN[k].x - cP[k].y);
+        // x: differences at both pairs, then the two rows of each face
+        const Q aPp = A0[hL + 1], aPm = A0[hL - 1], aNp = A0[hN + 1], aNm = A0[hN - 1];
+        const Q bPp = B0[hL + 1], bPm = B0[hL - 1], bNp = B0[hN + 1], bNm = B0[hN - 1];
+        const V DP[4] = {vsub(aPp.a, aPm.a), vsub(aPp.b, aPm.b), vsub(bPp.a, bPm.a), vsub(bPp.b, bPm.b)};
+        const V DN[4] = {vsub(aNp.a, aNm.a), vsub(aNp.b, aNm.b), vsub(bNp.a, bNm.a), vsub(bNp.b, bNm.b)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t1[k] = vpair(DP[k].x + DP[k].y, DP[k].y + DN[k].x);
+        const Q aPu = AP[hL], aPd = AM[hL], aNu = AP[hN], aNd = AM[hN];
+        const Q bPu = BP[hL], bPd = BM[hL], bNu = BP[hN], bNd = BM[hN];
+        const V EP[4] = {vsub(aPu.a, aPd.a), vsub(aPu.b, aPd.b), vsub(bPu.a, bPd.a), vsub(bPu.b, bPd.b)};
+        const V EN[4] = {vsub(aNu.a, aNd.a), vsub(aNu.b, aNd.b), vsub(bNu.a, bNd.a), vsub(bNu.b, bNd.b)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t2[k] = vpair(EP[k].x + EP[k].y, EP[k].y + EN[k].x);
+        const Q cP_ = C0[hL], cN_ = C0[hN];
+        const V dP = D0[rL], dN = D0[rL + RX];
+        const V f = vmul(K.half, vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
+        const V cs = vmul(K.half, vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x));
+        const V cl = vmul(K.half, vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x));
+        face_flux(K, f, cs, cl, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
+    };
+    // z face between planes z and z+1 of the pair at h (ring index r)
+    auto zface = [&](int z, int h, int r, V& Fc, V& Fd) {
+        const Q* A0 = sA + (z & 3) * HP;
+        const Q* A1 = sA + ((z + 1) & 3) * HP;
+        const Q* B0 = sB + (z & 3) * HP;
+        const Q* B1 = sB + ((z + 1) & 3) * HP;
+        const Q* C0 = sC + slot3(z) * HP;
+        const Q* C1 = sC + slot3(z + 1) * HP;
+        const V* D0 = sD + (z & 1) * RP;
+        const V* D1 = sD + ((z + 1) & 1) * RP;
+        const Q a0 = A0[h], a1 = A1[h], b0 = B0[h], b1 = B1[h];
+        V n[4] = {vsub(a1.a, a0.a), vsub(a1.b, a0.b), vsub(b1.a, b0.a), vsub(b1.b, b0.b)};
+        V t1[4], t2[4];
+        {
+            const Q ap0 = A0[h + 1], am0 = A0[h - 1], ap1 = A1[h + 1], am1 = A1[h - 1];
+            const Q bp0 = B0[h + 1], bm0 = B0[h - 1], bp1 = B1[h + 1], bm1 = B1[h - 1];
+            t1[0] = vsub(vadd(ap0.a, ap1.a), vadd(am0.a, am1.a));
+            t1[1] = vsub(vadd(ap0.b, ap1.b), vadd(am0.b, am1.b));
+            t1[2] = vsub(vadd(bp0.a, bp1.a), vadd(bm0.a, bm1.a));
+            t1[3] = vsub(vadd(bp0.b, bp1.b), vadd(bm0.b, bm1.b));
+        }
+        {
+            const Q aS0 = A0[h - HX], aS1 = A1[h - HX], aN0 = A0[h + HX], aN1 = A1[h + HX];
+            const Q bS0 = B0[h - HX], bS1 = B1[h - HX], bN0 = B0[h + HX], bN1 = B1[h + HX];
+            const V SP[4] = {vadd(a0.a, a1.a), vadd(a0.b, a1.b), vadd(b0.a, b1.a), vadd(b0.b, b1.b)};
+            const V SS[4] = {vadd(aS0.a, aS1.a), vadd(aS0.b, aS1.b), vadd(bS0.a, bS1.a), vadd(bS0.b, bS1.b)};
+            const V SN[4] = {vadd(aN0.a, aN1.a), vadd(aN0.b, aN1.b), vadd(bN0.a, bN1.a), vadd(bN0.b, bN1.b)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t2[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
+        }
+        const Q c0 = C0[h], c1 = C1[h];
+        face_flux(K, vmul(K.half, vadd(a0.a, a1.a)), vmul(K.half, vadd(c0.a, c1.a)), vmul(K.half, vadd(c0.b, c1.b)),
+                  vadd(D0[r], D1[r]), n, t1, t2, Fc, Fd);
+    };
+    auto z_noflux = [&](int z) {
+        return (z == -1 && G.bc_lo[2] == BC_NOFLUX) || (z == nz - 1 && G.bc_hi[2] == BC_NOFLUX);
     };
 
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(nz, z0 + zchunk);
     if (z0 >= z1) return;
 
-    // prologue: planes z0-2 .. z0+1, rates of z0-1 and z0, z faces (z0-1, z0);
-    // plane z0+1 reuses the {c_s, c_l}/phi slot of z0-2, so it comes after rates(z0-1)
+    // prologue: planes z0-2 .. z0+1 into the rings, rates of z0-1 and z0, the
+    // z face (z0-1, z0).  The single staging slot is refilled only after a
+    // barrier has ordered every read of it.
     for (int z = z0 - 2; z <= z0; ++z) {
         fetch_plane(z);
+        cp_async_commit();
+        cp_async_wait_all();
         store_plane(z);
+        __syncthreads();
     }
-    fetch_plane(z0 + 1);
-    __syncthreads();
     rates_plane(z0 - 1);
-    __syncthreads();
+    fetch_plane(z0 + 1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();   // plane z0+1 reuses the {c_s, c_l} / phi slots of z0-2
     store_plane(z0 + 1);
-    fetch_plane(z0 + 2);
     __syncthreads();
     rates_plane(z0);
-    __syncthreads();
-    faces_plane(z0 - 1);     // x/y faces of plane z0-1 are computed and unused
-    __syncthreads();
-    V2<T> fz_down = sFz[tid];
+    fetch_plane(z0 + 2);
+    cp_async_commit();
+    V fzc_down, fzd_down;
+    zface(z0 - 1, own_h, own_r, fzc_down, fzd_down);
+    if (z_noflux(z0 - 1)) fzc_down = fzd_down = vpair(T(0), T(0));
+    __syncthreads();   // the loop's first store reuses the {c_s, c_l} slot of z0-1
 
-    // own-cell state of the plane being updated, fetched one iteration ahead
-    T own_c = T(0), own_d = T(0), own_lo = T(0);
-    auto fetch_own = [&](int z) {
-        if (own_in && z < nz) {
-            const long long gi = (long long)z * sz + own_xy;
-            own_c = c_in[gi];
-            own_d = d_in[gi];
-            if (clo_in != nullptr) own_lo = clo_in[gi];
+    // fluxes of the plane being updated, carried from its faces phase to its update
+    V fxc, fxd, fyc, fyd, fzc, fzd;
+    // update of plane k from its fluxes and the own-cell state staged in sO
+    auto update = [&](int k) {
+        const Q left = sFx[ty * (TX + 1) + tx];
+        const T bc_ = sFy[2 * (ty * TX + tx)], bd_ = sFy[2 * (ty * TX + tx) + 1];
+        const V dFc = vadd(vadd(vsub(fxc, left.a), vpair(fyc.x - bc_, fyc.y - fyc.x)), vsub(fzc, fzc_down));
+        const V dFd = vadd(vadd(vsub(fxd, left.b), vpair(fyd.x - bd_, fyd.y - fyd.x)), vsub(fzd, fzd_down));
+        const V* O = reinterpret_cast<const V*>(sO);
+        const V c_k = O[tid], d_k = O[NT + tid];
+        const V phi_new = vfma(K.dt_dx2, sD[(k & 1) * RP + own_r], sA[(k & 3) * HP + own_h].a);
+        const V d_new = vfma(K.dt_dx2, dFd, d_k);
+        const V dcv = vmul(K.dt_dx2, dFc);
+        V c_new, lo_new;
+        if (clo_in != nullptr) {
+            // compensated (TwoSum) update of c = hi + lo
+            const V lo_k = O[2 * NT + tid];
+            const V s_ = vadd(c_k, dcv);
+            const V bv = vsub(s_, c_k);
+            const V err = vadd(vsub(c_k, vsub(s_, bv)), vsub(dcv, bv));
+            const V lo = vadd(lo_k, err);
+            c_new = vadd(s_, lo);
+            lo_new = vsub(lo, vsub(c_new, s_));
+        } else {
+            c_new = vadd(c_k, dcv);
+            lo_new = c_new;
         }
+        const long long gi = (long long)k * sz + own_xy;
+        if (in_lo) {
+            phi_out[gi] = phi_new.x;
+            c_out[gi] = c_new.x;
+            d_out[gi] = d_new.x;
+            if (clo_out != nullptr) clo_out[gi] = lo_new.x;
+        }
+        if (in_hi) {
+            phi_out[gi + nx] = phi_new.y;
+            c_out[gi + nx] = c_new.y;
+            d_out[gi + nx] = d_new.y;
+            if (clo_out != nullptr) clo_out[gi + nx] = lo_new.y;
+        }
+        fzc_down = fzc;
+        fzd_down = fzd;
     };
-    fetch_own(z0);
 
+    // two phases per plane:
+    //   1: update(k-1) | plane k+2 from staging into the rings
+    //   2: copies of plane k+3 and of the own state of k in flight | rates of
+    //      plane k+1 (a thread's faces read only its own new rate) | faces of k
     for (int k = z0; k < z1; ++k) {
-        // plane k+2 arrived in registers during the previous iteration
+        cp_async_wait_all();
+        if (k > z0) update(k - 1);
         store_plane(k + 2);
-        const T c_k = own_c, d_k = own_d, lo_k = own_lo;
-        if (k + 1 < z1) {
-            fetch_plane(k + 3);      // in flight during the rest of this iteration
-            fetch_own(k + 1);
-        }
         __syncthreads();
+        if (k + 1 < z1) fetch_plane(k + 3);
+        fetch_own(k);
+        cp_async_commit();
         rates_plane(k + 1);
-        __syncthreads();
-        faces_plane(k);
-        __syncthreads();
-        const V2<T> fz_up = sFz[tid];
-        if (own_in) {
-            const V2<T> fxl = sFx[ty * (TX + 1) + tx], fxr = sFx[ty * (TX + 1) + tx + 1];
-            const V2<T> fyl = sFy[ty * TX + tx], fyr = sFy[(ty + 1) * TX + tx];
-            const T dc = (fxr.x - fxl.x) + (fyr.x - fyl.x) + (fz_up.x - fz_down.x);
-            const T dd = (fxr.y - fxl.y) + (fyr.y - fyl.y) + (fz_up.y - fz_down.y);
-            const long long gi = (long long)k * sz + own_xy;
-            const T dtdx = C.dt * C.inv_dx;
-            const T dcv = dtdx * dc;
-            phi_out[gi] = sG4[(k & 3) * L::HP + own_h].x + C.dt * sPd[(k & 1) * L::RP + own_r];
-            d_out[gi] = d_k + dtdx * dd;
-            if (clo_in != nullptr) {
-                // compensated (TwoSum) update of c = hi + lo
-                const T s = c_k + dcv;
-                const T bv = s - c_k;
-                const T err = (c_k - (s - bv)) + (dcv - bv);
-                const T lo = lo_k + err;
-                const T hi = s + lo;
-                c_out[gi] = hi;
-                clo_out[gi] = lo - (hi - s);
-            } else {
-                c_out[gi] = c_k + dcv;
-            }
+        xface(k, own_h, own_r, fxc, fxd);
+        yface(k, own_h, own_r, fyc, fyd);
+        zface(k, own_h, own_r, fzc, fzd);
+        if (nf_x) fxc = fxd = vpair(T(0), T(0));
+        fyc = vmask(fyc, nf_ylo, nf_yhi);
+        fyd = vmask(fyd, nf_ylo, nf_yhi);
+        if (z_noflux(k)) fzc = fzd = vpair(T(0), T(0));
+        sFx[ty * (TX + 1) + tx + 1] = Q{fxc, fxd};
+        sFy[2 * ((ty + 1) * TX + tx)] = fyc.y;
+        sFy[2 * ((ty + 1) * TX + tx) + 1] = fyd.y;
+        if (tid < TYP) {
+            // x faces on the tile's low x edge, pair row tid
+            V ec, ed;
+            xface(k, (tid + 1) * HX + 1, (tid + 1) * RX, ec, ed);
+            if (nf_x_edge) ec = ed = vpair(T(0), T(0));
+            sFx[tid * (TX + 1)] = Q{ec, ed};
+        } else if (tid >= 32 && tid < 32 + TX) {
+            // y face on the tile's low y edge (upper lane of the pair row below the tile)
+            const int ex = tid - 32;
+            V ec, ed;
+            yface(k, ex + 2, ex + 1, ec, ed);
+            sFy[2 * ex] = nf_y_edge ? T(0) : ec.y;
+            sFy[2 * ex + 1] = nf_y_edge ? T(0) : ed.y;
         }
-        fz_down = fz_up;
+        __syncthreads();
     }
+    cp_async_wait_all();
+    update(z1 - 1);
 }
 
-template <typename T, int TX, int TY, int MINB>
-cudaError_t launch_step3d_tile(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K) {
-    using L = Tile3<T, TX, TY>;
-    auto kern = step3d_kernel<T, TX, TY, MINB>;
+// FP64 host value of p(phi) for the Dirichlet ghost state
+static double p_host3(const HostProblem& P, double f) {
+    const double g = f * (1.0 - f);
+    const double h = (P.interp == 1) ? f * f * (3.0 - 2.0 * f) : f * f * f * (6.0 * f * f - 15.0 * f + 10.0);
+    return h + P.a * (f - 0.5) * g * g;
+}
+
+template <typename V, typename T>
+static V splat(double v) {
+    V r;
+    r.x = T(v);
+    r.y = T(v);
+    return r;
+}
+
+template <typename T>
+static PairConsts<typename Lanes<T>::V> make_pair_consts(const HostProblem& P, const Consts<T>& C) {
+    using V = typename Lanes<T>::V;
+    auto S = [](double v) { return splat<V, T>(v); };
+    PairConsts<V> K;
+    K.one = S(1); K.two = S(2); K.half = S(0.5); K.sixteenth = S(1.0 / 16); K.sixteenth_neg = S(-1.0 / 16);
+    K.third = S(1.0 / 3); K.sixth = S(1.0 / 6); K.four = S(4); K.six = S(6);
+    K.h2 = S(C.h2); K.h3 = S(C.h3); K.h4 = S(C.h4); K.h5 = S(C.h5);
+    K.dh1 = S(C.dh1); K.dh2 = S(C.dh2); K.dh3 = S(C.dh3); K.dh4 = S(C.dh4);
+    K.a_int = S(P.a);
+    K.Ms_c = S(C.Ms_c); K.Ms_0 = S(C.Ms_0); K.Ml_c = S(C.Ml_c); K.Ml_0 = S(C.Ml_0);
+    K.b = S(P.b); K.A = S(P.A); K.one_m_A = S(1.0 - P.A); K.half_one_m_A = S(0.5 * (1.0 - P.A));
+    K.one_m_ke = S(1.0 - P.k_e); K.log_ke = S(std::log(P.k_e));
+    const double dx2 = P.dx * P.dx;
+    K.sigma = S(P.sigma); K.H = S(P.H); K.dx2 = S(dx2); K.inv_Mphi = S(1.0 / P.M_phi);
+    K.K_anti = S((1.0 - P.A) * (1.0 - P.A) * P.b * 4.0 * dx2);
+    K.delta2_dx2 = S(P.delta * P.delta * dx2);
+    K.delta2_4dx2 = S(4.0 * P.delta * P.delta * dx2);
+    K.dt_dx2 = S(P.dt / dx2);
+    return K;
+}
+
+template <typename T>
+static GridConsts<T> make_grid_consts(const HostProblem& P, const Clock<T>& Kc) {
+    GridConsts<T> G;
+    for (int a = 0; a < 3; ++a) {
+        G.n[a] = (int)P.n[a];
+        G.bc_lo[a] = P.bc_lo[a];
+        G.bc_hi[a] = P.bc_hi[a];
+    }
+    G.dx = T(P.dx);
+    G.theta0 = Kc.theta0;
+    G.G_theta = T(P.G_theta);
+    const double pg = p_host3(P, P.dir_phi);
+    G.dir_phi = T(P.dir_phi);
+    G.dir_c = T(pg * P.dir_cs + (1.0 - pg) * P.dir_cl);
+    G.dir_d = T(P.dir_cs - P.dir_cl);
+    return G;
+}
+
+// planes per CTA: minimise (waves of resident CTAs) x (planes + prologue) over
+// the number of z chunks, so that small grids still fill every SM
+static int choose_zchunk(long long tiles, int nz, long long resident) {
+    int best = nz;
+    double best_cost = 1e300;
+    for (int chunks = 1; chunks <= std::max(1, nz / 8); ++chunks) {
+        const int zc = (nz + chunks - 1) / chunks;
+        const long long nch = (nz + zc - 1) / zc;
+        const long long waves = (tiles * nch + resident - 1) / resident;
+        const double cost = (double)waves * (zc + 3.0);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
+}
+
+template <typename T>
+cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& Kc) {
+    constexpr int TX = 32, TY = 16;
+    using L = PTile<T, TX, TY>;
+    auto k19 = step3d_kernel<T, TX, TY, true>;
+    auto k7 = step3d_kernel<T, TX, TY, false>;
     static bool configured = false;
     static int per_sm = 1, sms = 1;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+        cudaError_t e = cudaFuncSetAttribute(k19, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L::NT, L::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k19, L::NT, L::BYTES);
         if (per_sm < 1) per_sm = 1;
         configured = true;
     }
+    const HostProblem& P = *a.prob;
+    const PairConsts<typename L::V> K = make_pair_consts<T>(P, C);
+    const GridConsts<T> G = make_grid_consts<T>(P, Kc);
     dim3 block(L::NT);
     dim3 grid((C.n[0] + TX - 1) / TX, (C.n[1] + TY - 1) / TY, 1);
     int zchunk = a.zchunk;
-    if (zchunk <= 0) {
-        const long long tiles = (long long)grid.x * grid.y;
-        const long long want = 4LL * per_sm * sms;
-        const int chunks = (int)std::max(1LL, (want + tiles - 1) / tiles);
-        zchunk = std::max(8, (C.n[2] + chunks - 1) / chunks);
-    }
+    if (zchunk <= 0) zchunk = choose_zchunk((long long)grid.x * grid.y, C.n[2], (long long)per_sm * sms);
     grid.z = (C.n[2] + zchunk - 1) / zchunk;
+    auto kern = (C.lap == 19) ? k19 : k7;
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
-        static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), C, K, zchunk);
+        static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step3d_tile<float, 32, 8, 4>(const StepLaunch&, const Consts<float>&,
-                                                         const Clock<float>&);
-template cudaError_t launch_step3d_tile<double, 32, 8, 2>(const StepLaunch&, const Consts<double>&,
-                                                          const Clock<double>&);
-
-size_t step3d_smem_bytes(int precision) {
-    return precision == 1 ? Tile3<double, 32, 8>::BYTES : Tile3<float, 32, 8>::BYTES;
-}
+template cudaError_t launch_step3d<float>(const StepLaunch&, const Consts<float>&, const Clock<float>&);
+template cudaError_t launch_step3d<double>(const StepLaunch&, const Consts<double>&, const Clock<double>&);
 
 }  // namespace pf
