@@ -65,11 +65,11 @@ SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 # sources the capture ran.  The figure is reported as null as soon as those
 # sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (181.988864e6 + 143.170560e6) / 224 ** 3,
-    "captured_grid": 224,
+    "bytes_per_cell_update": (280.422400e6 + 229.353472e6) / 256 ** 3,
+    "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_internal.cuh", "pf_kernels.h"),
-    "sha256": ("0f62f2fbe9700dd8aaa9676e1447eb602669d994a5b2962129b6c464cf4acf58",
-               "ffdc389efafe89f3717680b7f2777ee9aaf7cd0de04f3e905dcde7f6b84b7089",
+    "sha256": ("f795c54d9ceee6349b22091fb4e0054f4bdb7039194f554652b2c673283a7c4e",
+               "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60",
                "6f2b278b5cc421adbf544bb59fc1386d67b011600adc02e65bcfb5f7ad7347a0"),
 }
 
@@ -355,9 +355,10 @@ def main():
         alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         achieved_tops = OPS_PER_CELL_UPDATE * cells / launch_s / 1e12
         traffic = step3d_traffic(cells)
-        traffic_note = (f"ncu DRAM bytes of one launch at {TRAFFIC_CAPTURE['captured_grid']}^3, "
-                        f"scaled by cells to {n}^3" if traffic is not None else
-                        "kernel sources changed since the capture")
+        cap = TRAFFIC_CAPTURE["captured_grid"]
+        traffic_note = ("kernel sources changed since the capture" if traffic is None else
+                        f"ncu DRAM bytes of one launch at {cap}^3" +
+                        ("" if cap == n else f", scaled by cells to {n}^3"))
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
