@@ -266,6 +266,58 @@ def run_kv_sweep(args):
     return 0
 
 
+def adjoint_inputs(n_inst=16, n=2048, A=1.1, b=1.0):
+    """16 pulled fronts of 2048 cells, V log-spaced in 0.05..5 (scaled), the
+    frozen gradient of the k(V) sweep; target k(V) = (k_e + V/V_D)/(1 + V/V_D),
+    V_D = 1 (the velocity-dependent partition law the calibration fits)."""
+    vs = np.logspace(np.log10(0.05), np.log10(5.0), n_inst)
+    prs, phis, css, cls = [], [], [], []
+    for v in vs:
+        pr, phi, cs, cl = wl.pulled_front_1d(N=n, dx=0.5, V=float(v), G_theta=5.25e-3, front_cell=256,
+                                             A=A, b=b)
+        prs.append(pr)
+        phis.append(phi)
+        css.append(cs)
+        cls.append(cl)
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    k_e = prs[0]["k_e"]
+    k_target = (k_e + vs) / (1.0 + vs)
+    return [n] * n_inst, vs, prs, dts, np.concatenate(phis), np.concatenate(css), np.concatenate(cls), k_target
+
+
+def run_adjoint(args):
+    """Cost of the parameter derivatives d k_i / d(M_phi, A, b) (pf_adjoint, FP32
+    value + derivative) against the forward run alone (pf_run_batch, same steps)."""
+    from paper_2303_09671_gb300 import pf
+    lengths, vs, prs, dts, phi, cs, cl, kt = adjoint_inputs()
+    K = args.steps
+    f32 = [a.astype(np.float32) for a in (phi, cs, cl)]
+    spl = max(1, K // 4)
+    fw = dict(dt=dts, max_steps=K, steps_per_launch=spl, launches_per_graph=4, check_every=K, tol=-1.0)
+    pf.run_batch(prs[0], lengths, vs, *f32, **dict(fw, max_steps=spl, launches_per_graph=1))   # warm-up
+    t0 = time.perf_counter()
+    fwd = pf.run_batch(prs[0], lengths, vs, *f32, **fw)
+    fwd_wall = time.perf_counter() - t0
+    pf.adjoint(prs[0], lengths, vs, *f32, spl, k_target=kt, dt=dts, steps_per_launch=spl)       # warm-up
+    t0 = time.perf_counter()
+    adj = pf.adjoint(prs[0], lengths, vs, *f32, K, k_target=kt, dt=dts, steps_per_launch=spl)
+    adj_wall = time.perf_counter() - t0
+    ratio = adj["gpu_ms"] / fwd["gpu_ms"]
+    out = {"metric": "adjoint/forward cost ratio (d k_i / d(M_phi, A, b), 16 pulled fronts x 2048 cells)",
+           "value": ratio, "unit": "ratio of device times", "n_gpus": 1, "steps": K,
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "16 1D pulled fronts x 2048 cells, V log-spaced 0.05..5, G=5.25e-3, "
+                                  "A=1.1, b=1, k_target=(k_e+V)/(1+V)",
+                      "parameters": list(pf.ADJ_PARAMS)},
+           "forward_gpu_s": fwd["gpu_ms"] * 1e-3, "forward_wall_s": fwd_wall,
+           "adjoint_gpu_s": adj["gpu_ms"] * 1e-3, "adjoint_wall_s": adj_wall,
+           "wall_ratio": adj_wall / fwd_wall,
+           "k_forward_vs_adjoint_max_abs": float(np.abs(fwd["k_v"] - adj["k"]).max()),
+           "loss": adj["loss"], "grad": [float(g) for g in adj["grad"]]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,11 +327,13 @@ def main():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "kv-sweep"])
+    ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "kv-sweep", "adjoint"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "kv-sweep":
         return run_kv_sweep(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.impl == "reference":
         return run_reference(args)
 

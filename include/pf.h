@@ -219,6 +219,48 @@ typedef struct {
  * memory; synchronises `stream`.  Returns PF_EINVAL for invalid descriptors. */
 int pf_run_batch(const pf_batch_desc* desc, pf_batch_result* res, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Parameter sensitivities of the pulled-front partition coefficient, for
+ * calibrating the trapping parameter A, the mobility shape b and the
+ * phase-field mobility M_phi against a k(V) target (the tuning of A, b and W
+ * of Sec. "Tailoring the partition coefficient: Selection of A").
+ *
+ * For every instance of `batch` (same meaning as for pf_run_batch; the
+ * k_v-convergence fields are ignored) the run takes exactly `nsteps` steps
+ * and evaluates k_i = c_inf / max_x c, c = p c_s + (1-p) c_l, at the end.
+ * The derivatives dk_i/dtheta are exact derivatives of the discrete run
+ * (tangent-linear: the state is carried as value + derivative along one
+ * parameter, one CTA per instance and parameter, all concurrent); at the
+ * maximum the derivative of the maximising cell is taken (a subgradient where
+ * two cells tie).  With k_target given, the loss is
+ *   L = sum_i (k_i - k_target_i)^2,  dL/dtheta = sum_i 2 (k_i - k_target_i) dk_i/dtheta.
+ * batch.params.precision selects FP32 or FP64 arithmetic for value and
+ * derivative; instances hold at most 4096 (FP32) or 2048 (FP64) cells.
+ * ------------------------------------------------------------------------ */
+enum { PF_ADJ_MPHI = 1, PF_ADJ_A = 2, PF_ADJ_B = 4 };
+
+typedef struct {
+    pf_batch_desc batch;      /* instances, initial fields, shared parameters */
+    int64_t nsteps;           /* steps per instance (> 0) */
+    int wrt;                  /* parameters to differentiate: PF_ADJ_* bits (non-zero) */
+    const double* k_target;   /* per instance, host; NULL: loss and grad are 0 */
+} pf_adjoint_desc;
+
+typedef struct {
+    double* k;                /* optional [n_instances]: k_i after nsteps */
+    double* dk;               /* optional [3 * n_instances]: dk_i/d(M_phi, A, b) at
+                                 dk[3 i + j]; 0 for parameters not in wrt */
+    double loss;              /* L (0 without k_target) */
+    double grad[3];           /* dL/d(M_phi, A, b) (0 outside wrt or without k_target) */
+    double gpu_ms;            /* device time of the stepping (CUDA events) */
+} pf_adjoint_result;
+
+/* Run the instances with derivatives and fill `res`.  Caller-owned host
+ * arrays; allocates and frees its own device memory; synchronises `stream`.
+ * PF_EINVAL for invalid descriptors (empty wrt, nsteps <= 0, instance too long,
+ * the conditions of pf_run_batch). */
+int pf_adjoint(const pf_adjoint_desc* desc, pf_adjoint_result* res, void* stream);
+
 /* Allocation-free FP64 free energy and total solute (the paper has no
  * counterpart: this is a service for callers that cannot allocate device
  * memory -- a process whose device memory is held by another allocator, a

@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 #include "pf.h"
+#include "pf_dual.cuh"
 #include "pf_internal.cuh"
 #include "pf_kernels.h"
 
@@ -371,6 +372,7 @@ cudaError_t set_smem_limits(size_t* max_dynamic) {
 
 struct Group {
     int nt;
+    int dir = -1;      // seeded parameter of a tangent run (0 M_phi, 1 A, 2 b), -1 none
     int nmax;
     std::vector<int> ids;
     int* d_ids = nullptr;
@@ -390,6 +392,7 @@ struct BatchRun {
     BatchState* st = nullptr;
     double *dv = nullptr, *ddt = nullptr;
     std::vector<Group> groups;
+    std::vector<int> rep_dir;   // tangent runs: seeded parameter of each instance
     cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
     int64_t launches = 0;
 
@@ -433,6 +436,16 @@ struct BatchRun {
         const double pg = p_of_host(P, D.bc.dir_phi);
         a.fc = T(pg * D.bc.dir_cs + (1.0 - pg) * D.bc.dir_cl);
         a.fd = T(D.bc.dir_cs - D.bc.dir_cl);
+        if constexpr (IsDual<T>::value) {
+            // seed d/dtheta = 1 on the parameter of this group
+            using VT = decltype(C.A.v);
+            if (g.dir == 0) C.inv_Mphi = make_dual<VT>(VT(1.0 / P.M_phi), VT(-1.0 / (P.M_phi * P.M_phi)));
+            if (g.dir == 1) {
+                C.A = make_dual<VT>(VT(P.A), VT(1));
+                C.one_m_A = make_dual<VT>(VT(1.0 - P.A), VT(-1));
+            }
+            if (g.dir == 2) C.b = make_dual<VT>(VT(P.b), VT(1));
+        }
         return a;
     }
 
@@ -455,11 +468,13 @@ struct BatchRun {
             if (g.done) cudaEventDestroy(g.done);
         }
         groups.clear();
-        std::map<int, Group> by;
+        std::map<std::pair<int, int>, Group> by;
         for (int i = 0; i < D.n_instances; ++i) {
             const int nt = threads_for(D.n[i], cpt);
-            Group& g = by[nt];
+            const int dir = rep_dir.empty() ? -1 : rep_dir[i];
+            Group& g = by[{nt, dir}];
             g.nt = nt;
+            g.dir = dir;
             g.nmax = std::max(g.nmax, (int)D.n[i]);
             g.ids.push_back(i);
         }
@@ -480,6 +495,25 @@ struct BatchRun {
 
 }  // namespace
 
+// per-instance time step: the given one, or 0.9 of the stable step capped so
+// that the window moves at most half a cell per step
+static bool batch_time_steps(const pf_batch_desc& D, std::vector<double>& out, std::string& err) {
+    pf_grid g1{1, {8, 1, 1}, D.dx};
+    double dts = 0;
+    pf_stable_dt(&g1, &D.params, &dts);
+    out.resize(D.n_instances);
+    for (int i = 0; i < D.n_instances; ++i) {
+        double dt = (D.dt && D.dt[i] > 0) ? D.dt[i] : 0.9 * dts;
+        if (!(D.dt && D.dt[i] > 0) && D.v_pull[i] > 0) dt = std::min(dt, 0.5 * D.dx / D.v_pull[i]);
+        if (!(dt > 0) || dt > dts * (1 + 1e-12) || D.v_pull[i] * dt >= D.dx) {
+            err = "invalid or unstable time step for instance " + std::to_string(i);
+            return false;
+        }
+        out[i] = dt;
+    }
+    return true;
+}
+
 template <typename T>
 static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t main, std::string& err) {
     BatchRun<T> B(D, main, err);
@@ -490,19 +524,7 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
         B.off[i] = B.total;
         B.total += D.n[i];
     }
-    // time steps
-    pf_grid g1{1, {8, 1, 1}, D.dx};
-    double dts = 0;
-    pf_stable_dt(&g1, &D.params, &dts);
-    for (int i = 0; i < N; ++i) {
-        double dt = (D.dt && D.dt[i] > 0) ? D.dt[i] : 0.9 * dts;
-        if (!(D.dt && D.dt[i] > 0) && D.v_pull[i] > 0) dt = std::min(dt, 0.5 * D.dx / D.v_pull[i]);
-        if (!(dt > 0) || dt > dts * (1 + 1e-12) || D.v_pull[i] * dt >= D.dx) {
-            err = "invalid or unstable time step for instance " + std::to_string(i);
-            return PF_EINVAL;
-        }
-        B.dt[i] = dt;
-    }
+    if (!batch_time_steps(D, B.dt, err)) return PF_EINVAL;
     const size_t fb = (size_t)B.total * sizeof(T);
     cudaError_t e = cudaMalloc(&B.phi, fb);
     if (e == cudaSuccess) e = cudaMalloc(&B.c, fb);
@@ -749,6 +771,254 @@ int run_batch(const pf_batch_desc* D, pf_batch_result* R, void* stream, std::str
     return run_batch_forked<float>(*D, R, s, err);
 }
 
+
+// ------------------------------------------------------------------ tangents
+// packed value state (phi, c, d) of the instances -> the Dual state of every
+// (direction, instance) replica, derivative 0 (the initial fields do not
+// depend on the parameters)
+template <typename V>
+__global__ void adjoint_replicate(const V* __restrict__ phi, const V* __restrict__ c, const V* __restrict__ d,
+                                  long long total, int reps, Dual<V>* P, Dual<V>* Cc, Dual<V>* Dd) {
+    const long long n = total * reps;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long s = k % total;
+        P[k] = make_dual<V>(phi[s], V(0));
+        Cc[k] = make_dual<V>(c[s], V(0));
+        Dd[k] = make_dual<V>(d[s], V(0));
+    }
+}
+
+// per replica: max_x c and the derivative of c at the maximising cell (lowest
+// index among ties)
+template <typename V>
+__global__ void __launch_bounds__(256) adjoint_cmax(const Dual<V>* __restrict__ c, const BatchState* __restrict__ st,
+                                                    double* __restrict__ out) {
+    const BatchState S = st[blockIdx.x];
+    double best = -INFINITY, tan = 0.0;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
+        const Dual<V> x = c[S.off + i];
+        const double v = (double)x.v;
+        if (v > best || (v == best && i < bi)) {
+            best = v;
+            tan = (double)x.t;
+            bi = i;
+        }
+    }
+    __shared__ double sb[256], st_[256];
+    __shared__ int si[256];
+    sb[threadIdx.x] = best;
+    st_[threadIdx.x] = tan;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            const double vb = sb[threadIdx.x + o];
+            const int ib = si[threadIdx.x + o];
+            if (vb > sb[threadIdx.x] || (vb == sb[threadIdx.x] && ib < si[threadIdx.x])) {
+                sb[threadIdx.x] = vb;
+                st_[threadIdx.x] = st_[threadIdx.x + o];
+                si[threadIdx.x] = ib;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = sb[0];
+        out[2 * blockIdx.x + 1] = st_[0];
+    }
+}
+
+template <typename V>
+static int run_adjoint_T(const pf_adjoint_desc& A, pf_adjoint_result* R, cudaStream_t main, std::string& err) {
+    using T = Dual<V>;
+    const pf_batch_desc& D = A.batch;
+    const int N = D.n_instances;
+    std::vector<int> dirs;
+    for (int j = 0; j < 3; ++j)
+        if ((A.wrt >> j) & 1) dirs.push_back(j);
+    const int ND = (int)dirs.size();
+    const int M = N * ND;
+    // replicas r = q N + i: instance i, parameter dirs[q]
+    std::vector<int64_t> rn(M);
+    std::vector<double> rv(M), rdt(M);
+    std::vector<int> rdir(M);
+    std::vector<double> dt1;
+    if (!batch_time_steps(D, dt1, err)) return PF_EINVAL;
+    for (int q = 0; q < ND; ++q)
+        for (int i = 0; i < N; ++i) {
+            rn[q * N + i] = D.n[i];
+            rv[q * N + i] = D.v_pull[i];
+            rdt[q * N + i] = dt1[i];
+            rdir[q * N + i] = dirs[q];
+        }
+    pf_batch_desc RD = D;
+    RD.n_instances = M;
+    RD.n = rn.data();
+    RD.v_pull = rv.data();
+    RD.dt = rdt.data();
+    RD.check_every = 0;   // fixed number of steps, no convergence test
+    BatchRun<T> B(RD, main, err);
+    B.rep_dir = rdir;
+    B.off.resize(M);
+    B.dt = rdt;
+    int64_t total1 = 0;
+    for (int i = 0; i < N; ++i) total1 += D.n[i];
+    for (int r = 0; r < M; ++r) {
+        B.off[r] = B.total;
+        B.total += rn[r];
+    }
+    const size_t fb = (size_t)B.total * sizeof(T), vb = (size_t)total1 * sizeof(V);
+    V *vphi = nullptr, *vcs = nullptr, *vcl = nullptr, *vc = nullptr, *vd = nullptr;
+    double* dout = nullptr;
+    cudaError_t e = cudaMalloc(&B.phi, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.c, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.d, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.st, M * sizeof(BatchState));
+    if (e == cudaSuccess) e = cudaMalloc(&B.dv, M * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&B.ddt, M * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&vphi, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&vcs, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&vcl, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&vc, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&vd, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 2 * M * sizeof(double));
+    auto free_tmp = [&] {
+        void* ptrs[] = {vphi, vcs, vcl, vc, vd, dout};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    };
+    if (e != cudaSuccess) {
+        free_tmp();
+        cudaGetLastError();
+        err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return PF_ENOMEM;
+    }
+    std::vector<BatchState> hs(M);
+    for (int r = 0; r < M; ++r) hs[r] = BatchState{B.off[r], (int)rn[r], 0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+    e = cudaMemcpyAsync(vphi, D.phi0, vb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vcs, D.cs0, vb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vcl, D.cl0, vb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.st, hs.data(), M * sizeof(BatchState), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.dv, rv.data(), M * sizeof(double), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.ddt, rdt.data(), M * sizeof(double), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) {
+        batch_to_state<V><<<1216, 256, 0, main>>>(vcs, vcl, vphi, vc, vd, total1, D.params.interp, D.params.a);
+        adjoint_replicate<V><<<1216, 256, 0, main>>>(vphi, vc, vd, total1, ND, B.phi, B.c, B.d);
+        e = cudaGetLastError();
+    }
+    size_t max_dyn = 0;
+    if (e == cudaSuccess) e = set_smem_limits<T>(&max_dyn);
+    if (e == cudaSuccess) {
+        int64_t nbig = 0;
+        for (int i = 0; i < N; ++i) nbig = std::max(nbig, (int64_t)D.n[i]);
+        if ((size_t)6 * nbig * sizeof(T) > max_dyn) {
+            free_tmp();
+            err = "longest instance does not fit in shared memory";
+            return PF_EINVAL;
+        }
+    }
+    const int cpt = D.cells_per_thread > 0 ? D.cells_per_thread : 8;
+    if (e == cudaSuccess) e = B.make_groups(cpt);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&B.t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&B.t1);
+    const int64_t chunk = D.steps_per_launch > 0 ? D.steps_per_launch : A.nsteps;
+    if (e == cudaSuccess) e = cudaEventRecord(B.t0, main);
+    for (int64_t done = 0; done < A.nsteps && e == cudaSuccess; done += chunk)
+        e = B.issue((int)std::min(chunk, A.nsteps - done));
+    if (e == cudaSuccess) e = cudaEventRecord(B.t1, main);
+    if (e == cudaSuccess) {
+        adjoint_cmax<V><<<M, 256, 0, main>>>(B.c, B.st, dout);
+        e = cudaGetLastError();
+    }
+    std::vector<double> hout(2 * M);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout.data(), dout, 2 * M * sizeof(double), cudaMemcpyDeviceToHost, main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+    float ms = 0;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, B.t0, B.t1);
+    free_tmp();
+    if (e != cudaSuccess) {
+        err = std::string("adjoint run: ") + cudaGetErrorString(e);
+        return PF_ECUDA;
+    }
+    // k_i = c_inf / c_max,i and dk_i = -c_inf dc_max,i / c_max,i^2; the loss
+    const double cinf = D.params.c_inf;
+    R->loss = 0.0;
+    R->grad[0] = R->grad[1] = R->grad[2] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double cm = hout[2 * i];
+        const double k = cinf / cm;
+        if (R->k) R->k[i] = k;
+        double dk[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < ND; ++q) dk[dirs[q]] = -cinf * hout[2 * (q * N + i) + 1] / (cm * cm);
+        if (R->dk)
+            for (int j = 0; j < 3; ++j) R->dk[3 * i + j] = dk[j];
+        if (A.k_target) {
+            const double res = k - A.k_target[i];
+            R->loss += res * res;
+            for (int j = 0; j < 3; ++j) R->grad[j] += 2.0 * res * dk[j];
+        }
+    }
+    R->gpu_ms = ms;
+    return PF_OK;
+}
+
+int run_adjoint(const pf_adjoint_desc* A, pf_adjoint_result* R, void* stream, std::string& err) {
+    if (!A || !R) { err = "null argument"; return PF_EINVAL; }
+    const pf_batch_desc& D = A->batch;
+    const pf_params& P = D.params;
+    if (A->nsteps <= 0 || A->nsteps > (int64_t(1) << 40)) { err = "nsteps must be positive"; return PF_EINVAL; }
+    if (A->wrt <= 0 || A->wrt > 7) { err = "wrt must be a non-empty set of PF_ADJ_* bits"; return PF_EINVAL; }
+    const int64_t nmax = (P.precision == PF_FP64) ? 2048 : 4096;
+    if (D.n_instances <= 0 || !D.n || !D.v_pull || !D.phi0 || !D.cs0 || !D.cl0) { err = "empty batch or null array"; return PF_EINVAL; }
+    for (int i = 0; i < D.n_instances; ++i) {
+        if (D.n[i] < 8 || D.n[i] > nmax) { err = "instance length outside 8.." + std::to_string(nmax); return PF_EINVAL; }
+        if (!(D.v_pull[i] >= 0) || !std::isfinite(D.v_pull[i])) { err = "negative or non-finite velocity"; return PF_EINVAL; }
+    }
+    if (!(D.dx > 0) || !(P.k_e > 0 && P.k_e < 1) || !(P.b > 0) || !(P.M_phi > 0) || !(P.H > 0) ||
+        !(P.sigma > 0) || !(P.D_s > 0) || !(P.D_l > 0) || !(P.c_inf > 0)) {
+        err = "invalid model parameters";
+        return PF_EINVAL;
+    }
+    if (P.precision != PF_FP32 && P.precision != PF_FP64) { err = "precision must be PF_FP32 or PF_FP64"; return PF_EINVAL; }
+    if (D.bc.lo[0] != PF_BC_NOFLUX || D.bc.hi[0] != PF_BC_DIRICHLET) {
+        err = "instances need a no-flux cold end and a Dirichlet hot end";
+        return PF_EINVAL;
+    }
+    if (!(D.bc.dir_cs > 0) || !(D.bc.dir_cl > 0)) { err = "Dirichlet concentrations must be positive"; return PF_EINVAL; }
+    const int cpt = D.cells_per_thread;
+    if (cpt != 0 && cpt != 1 && cpt != 2 && cpt != 4 && cpt != 8) { err = "cells_per_thread must be 0, 1, 2, 4 or 8"; return PF_EINVAL; }
+    for (int i = 0; i < D.n_instances; ++i)
+        if (D.n[i] > (int64_t)1024 * (cpt > 0 ? cpt : 8)) { err = "cells_per_thread too small for the longest instance"; return PF_EINVAL; }
+    if (D.steps_per_launch < 0 || D.steps_per_launch > (1 << 30)) { err = "steps_per_launch must be in 0..2^30"; return PF_EINVAL; }
+    if (D.steps_per_launch == 0 && A->nsteps > (1 << 30)) { err = "nsteps above 2^30 needs steps_per_launch"; return PF_EINVAL; }
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(work, ev, 0);
+    int rc = PF_ECUDA;
+    if (e == cudaSuccess) {
+        rc = (P.precision == PF_FP64) ? run_adjoint_T<double>(*A, R, work, err) : run_adjoint_T<float>(*A, R, work, err);
+        cudaError_t e2 = cudaEventRecord(ev, work);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(caller, ev, 0);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(work);
+        if (rc == PF_OK && e2 != cudaSuccess) {
+            err = std::string("adjoint join: ") + cudaGetErrorString(e2);
+            rc = PF_ECUDA;
+        }
+    } else {
+        err = std::string("adjoint stream: ") + cudaGetErrorString(e);
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (work) cudaStreamDestroy(work);
+    return rc;
+}
+
 }  // namespace pf
 
 namespace {
@@ -758,6 +1028,13 @@ thread_local std::string g_batch_error;
 extern "C" int pf_run_batch(const pf_batch_desc* desc, pf_batch_result* res, void* stream) {
     g_batch_error.clear();
     const int rc = pf::run_batch(desc, res, stream, g_batch_error);
+    if (rc != PF_OK) pf::set_create_error(g_batch_error);
+    return rc;
+}
+
+extern "C" int pf_adjoint(const pf_adjoint_desc* desc, pf_adjoint_result* res, void* stream) {
+    g_batch_error.clear();
+    const int rc = pf::run_adjoint(desc, res, stream, g_batch_error);
     if (rc != PF_OK) pf::set_create_error(g_batch_error);
     return rc;
 }

@@ -68,6 +68,20 @@ class pf_batch_result(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("gpu_ms", ctypes.c_double)]
 
 
+class pf_adjoint_desc(ctypes.Structure):
+    _fields_ = [("batch", pf_batch_desc), ("nsteps", ctypes.c_int64), ("wrt", ctypes.c_int),
+                ("k_target", ctypes.POINTER(ctypes.c_double))]
+
+
+class pf_adjoint_result(ctypes.Structure):
+    _fields_ = [("k", ctypes.POINTER(ctypes.c_double)), ("dk", ctypes.POINTER(ctypes.c_double)),
+                ("loss", ctypes.c_double), ("grad", ctypes.c_double * 3), ("gpu_ms", ctypes.c_double)]
+
+
+ADJ_MPHI, ADJ_A, ADJ_B = 1, 2, 4
+ADJ_PARAMS = ("M_phi", "A", "b")
+
+
 # exported symbols and their signatures (the header include/pf.h declares the same set)
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -84,6 +98,7 @@ _SIGS = {
     "pf_stable_dt": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_params),
                                     ctypes.POINTER(ctypes.c_double)]),
     "pf_run_batch": (ctypes.c_int, [ctypes.POINTER(pf_batch_desc), ctypes.POINTER(pf_batch_result), _VP]),
+    "pf_adjoint": (ctypes.c_int, [ctypes.POINTER(pf_adjoint_desc), ctypes.POINTER(pf_adjoint_result), _VP]),
     "pf_energy_solute_noalloc": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_bc),
                                                 ctypes.POINTER(pf_params), ctypes.c_int64, ctypes.c_int64,
                                                 _VP, _VP, _VP, _VP, _VP]),
@@ -295,6 +310,95 @@ def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt
     _check(lib().pf_run_batch(ctypes.byref(D), ctypes.byref(R), _VP(s)), None)
     out.update(cells_per_thread=R.cells_per_thread, launches=R.launches, gpu_ms=R.gpu_ms)
     return out
+
+
+def _batch_desc(pr, lengths, v_pull, phi0, cs0, cl0, precision, dt, keep):
+    N = len(lengths)
+    dtype = np.float64 if precision == "fp64" else np.float32
+    n_arr = np.ascontiguousarray(lengths, dtype=np.int64)
+    v_arr = np.ascontiguousarray(v_pull, dtype=np.float64)
+    dt_arr = np.ascontiguousarray(dt if dt is not None else np.zeros(N), dtype=np.float64)
+    fields = [np.ascontiguousarray(a, dtype=dtype) for a in (phi0, cs0, cl0)]
+    total = int(n_arr.sum())
+    for a in fields:
+        if a.shape != (total,):
+            raise ValueError("packed fields must have sum(lengths) entries")
+    keep.extend([n_arr, v_arr, dt_arr, *fields])
+    g, b, p = make_structs(dict(pr, n=(8,), shift=False, v_pull=0.0), precision)
+    D = pf_batch_desc()
+    D.n_instances = N
+    D.n = n_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    D.v_pull = v_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    D.dt = dt_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    D.phi0, D.cs0, D.cl0 = (a.ctypes.data for a in fields)
+    D.dx = float(pr["dx"])
+    D.bc = b
+    D.params = p
+    return D
+
+
+def adjoint(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, *, k_target=None,
+            wrt=("M_phi", "A", "b"), precision="fp32", dt=None, steps_per_launch=0,
+            cells_per_thread=0, stream=None):
+    """pf_adjoint: k_i = c_inf / max c after `nsteps` steps of every pulled front
+    and the exact derivatives dk_i/d(M_phi, A, b) of the discrete run.
+
+    Same instance description as run_batch.  Returns dict(k, dk (N x 3), loss,
+    grad (3,), gpu_ms); loss and grad are those of sum (k - k_target)^2.
+    """
+    keep = []
+    D = _batch_desc(pr, lengths, v_pull, phi0, cs0, cl0, precision, dt, keep)
+    D.steps_per_launch = int(steps_per_launch)
+    D.cells_per_thread = int(cells_per_thread)
+    N = len(lengths)
+    A = pf_adjoint_desc()
+    A.batch = D
+    A.nsteps = int(nsteps)
+    A.wrt = sum(1 << ADJ_PARAMS.index(w) for w in wrt)
+    kt = None
+    if k_target is not None:
+        kt = np.ascontiguousarray(k_target, dtype=np.float64)
+        if kt.shape != (N,):
+            raise ValueError("k_target needs one value per instance")
+        A.k_target = kt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    k = np.zeros(N)
+    dk = np.zeros(3 * N)
+    R = pf_adjoint_result()
+    R.k = k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    R.dk = dk.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    s = _current_stream() if stream is None else stream
+    _check(lib().pf_adjoint(ctypes.byref(A), ctypes.byref(R), _VP(s)), None)
+    return dict(k=k, dk=dk.reshape(N, 3), loss=R.loss, grad=np.array(R.grad[:]), gpu_ms=R.gpu_ms)
+
+
+def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, iters=50, lr=0.05,
+              wrt=("M_phi", "A", "b"), precision="fp32", dt=None, betas=(0.9, 0.999), eps=1e-8,
+              callback=None):
+    """Adam on the logarithms of the chosen parameters (M_phi, A, b > 0), each
+    iteration one pf_adjoint run; returns (parameters, history of losses)."""
+    idx = [ADJ_PARAMS.index(w) for w in wrt]
+    theta = np.log(np.array([pr[ADJ_PARAMS[j]] for j in idx], dtype=np.float64))
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    hist = []
+    cur = dict(pr)
+    for it in range(1, iters + 1):
+        for j, t in zip(idx, theta):
+            cur[ADJ_PARAMS[j]] = float(np.exp(t))
+        r = adjoint(cur, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target=k_target, wrt=wrt,
+                    precision=precision, dt=dt)
+        hist.append(r["loss"])
+        g = np.array([r["grad"][j] for j in idx]) * np.exp(theta)   # d/d(log theta)
+        m = betas[0] * m + (1 - betas[0]) * g
+        v = betas[1] * v + (1 - betas[1]) * g * g
+        mh = m / (1 - betas[0] ** it)
+        vh = v / (1 - betas[1] ** it)
+        theta = theta - lr * mh / (np.sqrt(vh) + eps)
+        if callback is not None:
+            callback(it, cur, r)
+    for j, t in zip(idx, theta):
+        cur[ADJ_PARAMS[j]] = float(np.exp(t))
+    return {w: cur[w] for w in wrt}, hist
 
 
 def energy_solute_noalloc(pr: dict, phi, cs, cl, out, precision="fp32", step=0, shifts=0, stream=None):

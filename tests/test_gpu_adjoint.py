@@ -1,0 +1,146 @@
+"""Parameter derivatives of the pulled-front partition coefficient (pf_adjoint):
+k_i = c_inf / max c after a fixed number of steps, differentiated with respect
+to M_phi, A and b, against central finite differences of the FP64 oracle and
+of the GPU forward run; the loss and its gradient; an Adam calibration."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09671_gb300 import workloads as wl
+from paper_2303_09671_gb300 import pf
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = ("M_phi", "A", "b")
+
+
+def inputs(lengths, vs, A=1.1, b=1.0, dx=0.5, front_cell=24):
+    """Pulled fronts from uniform c_s = k_e c_inf, c_l = c_inf.  These starts
+    blow up near t = 2 for |1 - A| >~ 0.3 whatever the time step (in the oracle
+    as on the GPU), so A stays within 1 +- 0.2; A = 1 itself is avoided because
+    k is not differentiable in A there."""
+    prs, phis, css, cls = [], [], [], []
+    for n, v in zip(lengths, vs):
+        pr, phi, cs, cl = wl.pulled_front_1d(N=n, dx=dx, V=v, A=A, b=b, front_cell=front_cell)
+        prs.append(pr)
+        phis.append(phi)
+        css.append(cs)
+        cls.append(cl)
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    return prs, dts, np.concatenate(phis), np.concatenate(css), np.concatenate(cls)
+
+
+def p_of(pr, f):
+    """p(phi) = h + a (phi - 1/2) phi^2 (1-phi)^2 with the quintic h."""
+    h = f ** 3 * (6 * f * f - 15 * f + 10)
+    return h + pr["a"] * (f - 0.5) * (f * (1 - f)) ** 2
+
+
+def k_oracle(prs, dts, lengths, phi, cs, cl, nsteps, **override):
+    """k_i = c_inf / max_x (p c_s + (1-p) c_l) of the FP64 oracle after nsteps."""
+    ks, o = [], 0
+    for pr, dt, n in zip(prs, dts, lengths):
+        q = dict(pr, dt=dt, **override)
+        st = oracle.State(q, phi[o:o + n], cs[o:o + n], cl[o:o + n])
+        st.step(nsteps)
+        p = p_of(q, st.phi)
+        ks.append(q["c_inf"] / np.max(p * st.cs + (1 - p) * st.cl))
+        o += n
+    return np.array(ks)
+
+
+def richardson(k_of, th, rel=1e-4):
+    """Central difference extrapolated from h and h/2, (4 D(h/2) - D(h)) / 3:
+    truncation O(h^4), and a rounding floor of about (run-to-run rounding of k)
+    / h ~ 1e-11, small enough for derivatives of order 1e-3 to be checked at
+    1e-6 relative (a plain difference at h = 1e-6 leaves ~1e-9 of rounding)."""
+    h = rel * abs(th)
+    d1 = (k_of(th + h) - k_of(th - h)) / (2 * h)
+    d2 = (k_of(th + h / 2) - k_of(th - h / 2)) / h
+    return (4 * d2 - d1) / 3
+
+
+def test_fp64_derivatives_match_oracle_finite_differences():
+    lengths, vs = [128, 200], [0.1, 0.3]
+    prs, dts, phi, cs, cl = inputs(lengths, vs)
+    nsteps = 400
+    r = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, nsteps, precision="fp64", dt=dts)
+    k0 = k_oracle(prs, dts, lengths, phi, cs, cl, nsteps)
+    assert np.abs(r["k"] - k0).max() <= 1e-11 * np.abs(k0).max()
+    for j, name in enumerate(PARAMS):
+        fd = richardson(lambda t: k_oracle(prs, dts, lengths, phi, cs, cl, nsteps, **{name: t}), prs[0][name])
+        scale = np.abs(fd).max()
+        assert scale > 0, name
+        err = np.abs(r["dk"][:, j] - fd).max() / scale
+        assert err <= 1e-6, (name, err, r["dk"][:, j], fd)
+
+
+def test_fp64_derivatives_match_gpu_finite_differences_and_forward_k():
+    lengths, vs = [256, 400, 640], [0.05, 0.2, 0.6]
+    prs, dts, phi, cs, cl = inputs(lengths, vs, A=1.2, b=0.8)
+    nsteps = 1000
+
+    def k_gpu(**override):
+        res = pf.run_batch(dict(prs[0], **override), lengths, vs, phi, cs, cl, precision="fp64", dt=dts,
+                           max_steps=nsteps, steps_per_launch=250, launches_per_graph=2,
+                           check_every=nsteps, tol=-1.0)
+        assert (res["steps"] == nsteps).all()
+        return res["k_v"]
+
+    r = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, nsteps, precision="fp64", dt=dts, steps_per_launch=300)
+    k0 = k_gpu()
+    assert np.abs(r["k"] - k0).max() <= 1e-12 * np.abs(k0).max()
+    for j, name in enumerate(PARAMS):
+        fd = richardson(lambda t: k_gpu(**{name: t}), prs[0][name])
+        err = np.abs(r["dk"][:, j] - fd).max() / np.abs(fd).max()
+        assert err <= 1e-6, (name, err)
+
+
+def test_fp32_derivatives_close_to_fp64():
+    lengths, vs = [300, 500], [0.1, 0.4]
+    prs, dts, phi, cs, cl = inputs(lengths, vs)
+    r64 = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 600, precision="fp64", dt=dts)
+    r32 = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 600, precision="fp32", dt=dts)
+    assert np.abs(r32["k"] - r64["k"]).max() <= 1e-5
+    for j in range(3):
+        err = np.abs(r32["dk"][:, j] - r64["dk"][:, j]).max() / np.abs(r64["dk"][:, j]).max()
+        assert err <= 1e-3, (PARAMS[j], err)
+
+
+def test_loss_gradient_and_parameter_subset():
+    lengths, vs = [128, 160, 192], [0.1, 0.2, 0.3]
+    prs, dts, phi, cs, cl = inputs(lengths, vs)
+    kt = np.array([0.3, 0.5, 0.7])
+    r = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 200, precision="fp64", dt=dts, k_target=kt)
+    res = r["k"] - kt
+    assert r["loss"] == pytest.approx(float((res ** 2).sum()), rel=1e-14)
+    np.testing.assert_allclose(r["grad"], (2 * res[:, None] * r["dk"]).sum(0), rtol=1e-13, atol=0)
+    # only A: the other columns are zero and the A column is unchanged
+    ra = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 200, precision="fp64", dt=dts, k_target=kt, wrt=("A",))
+    assert np.all(ra["dk"][:, [0, 2]] == 0) and ra["grad"][0] == 0 and ra["grad"][2] == 0
+    np.testing.assert_allclose(ra["dk"][:, 1], r["dk"][:, 1], rtol=1e-14, atol=0)
+
+
+def test_invalid_descriptors_rejected():
+    lengths, vs = [64], [0.1]
+    prs, dts, phi, cs, cl = inputs(lengths, vs)
+    with pytest.raises(pf.PFError):
+        pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 0, precision="fp64", dt=dts)
+    with pytest.raises(pf.PFError):
+        pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 10, precision="fp64", dt=dts, wrt=())
+    with pytest.raises(pf.PFError):
+        pf.adjoint(prs[0], [4096], vs, np.zeros(4096), np.ones(4096), np.ones(4096), 10,
+                   precision="fp64", dt=dts)
+
+
+def test_adam_calibration_lowers_the_loss():
+    """Targets from A = 1.15; Adam on A started from A = 1.05 reduces the loss."""
+    lengths, vs = [160, 200], [0.1, 0.3]
+    prs, dts, phi, cs, cl = inputs(lengths, vs, A=1.15)
+    nsteps = 300
+    kt = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, nsteps, precision="fp64", dt=dts)["k"]
+    start = dict(prs[0], A=1.05)
+    theta, hist = pf.calibrate(start, lengths, vs, phi, cs, cl, nsteps, kt, iters=12, lr=0.02,
+                               wrt=("A",), precision="fp64", dt=dts)
+    assert hist[-1] < 0.2 * hist[0], hist
+    assert abs(theta["A"] - 1.15) < abs(1.05 - 1.15)
