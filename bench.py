@@ -318,6 +318,59 @@ def run_adjoint(args):
     return 0
 
 
+def run_secondary(args):
+    """The other workload shapes of the paper on the same step (not the headline):
+    planar1d = 1D planar front, N = 1024, FP64, dx = W/4, the free energy F_h
+    read back every step (Sec. "Numerical technique"; latency-bound by design);
+    perturbed2d = 2D perturbed front 1024^2 FP32, 9-point Laplacian, periodic
+    along the front, no-flux across (state 16.8 MB: L2-resident)."""
+    import torch
+    from paper_2303_09671_gb300.pf import Sim
+    K, W = args.steps, max(args.warmup, 3)
+    stream = torch.cuda.Stream()
+    if args.workload == "planar1d":
+        pr, phi, cs, cl = wl.planar_1d(A=1.0, b=1.0)
+        prec, per_step_energy = "fp64", True
+        desc = "1D planar front N=1024 FP64 (k_e=0.1, u=0.3, D_s/D_l=1e-4, dx=W/4), F_h every step"
+    else:
+        pr, phi, cs, cl = wl.perturbed_front_2d(A=1.0, b=1.0)
+        prec, per_step_energy = "fp32", False
+        desc = ("2D perturbed front 1024^2 FP32 (k_e=0.15, u=0.3, D_s/D_l=1e-3, dx=W/2, 9-pt, "
+                "periodic along the front, no-flux across, 8 seeded modes, amplitude 2 cells)")
+    cells = int(np.prod(pr["n"]))
+    with torch.cuda.stream(stream):
+        sim = Sim(pr, prec, stream=stream.cuda_stream)
+        sim.set_fields(phi, cs, cl)
+        for _ in range(W):
+            sim.step(1)
+            if per_step_energy:
+                sim.energy()
+        stream.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        F = []
+        for _ in range(K):
+            sim.step(1)
+            if per_step_energy:
+                F.append(sim.energy())
+        ev1.record(stream)
+        ev1.synchronize()
+        wall = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        sim.close()
+    out = {"metric": f"phi/c_s/c_l cell-updates/s ({args.workload})", "value": cells * K / (ms * 1e-3),
+           "unit": "cell-updates/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
+           "higher_is_better": True, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": desc, "grid": list(pr["n"]), "per_step_energy": per_step_energy},
+           "wall_s": wall, "gpu_launches": K * (3 if per_step_energy else 1)}
+    if per_step_energy:
+        out["energy_non_increasing"] = bool(np.all(np.diff(F) <= 1e-12 * abs(F[0])))
+        out["steps_per_s"] = K / wall
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,13 +380,16 @@ def main():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "kv-sweep", "adjoint"])
+    ap.add_argument("--workload", default="sphere3d",
+                    choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "kv-sweep":
         return run_kv_sweep(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload in ("planar1d", "perturbed2d"):
+        return run_secondary(args)
     if args.impl == "reference":
         return run_reference(args)
 

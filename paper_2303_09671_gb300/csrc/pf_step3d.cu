@@ -12,7 +12,8 @@
 //   * shared memory holds the halo-2 tile of each plane as two-lane records
 //     {phi, Y}, {mu_s, mu_l}, {c_s, c_l} and phi (rings of 4, 4, 3 and 3
 //     planes), the phase-field rate on the halo-1 ring (2 planes) and the
-//     fluxes through the x faces and the upper y face of every cell pair;
+//     fluxes through the x faces and the upper y face of every cell pair; the
+//     next plane arrives by cp.async in a staging slot;
 //   * every thread evaluates the x+1/2, y+1/2 and z+1/2 faces of its own two
 //     cells, so the neighbour records the three faces share are read once;
 //     the faces on the tile's low x and low y edges are evaluated by one more
@@ -23,8 +24,8 @@
 //   * differences are kept in grid units (not divided by dx) and the stored
 //     rate is dx^2 dphi/dt, so that F_c, F_d below are dx times the fluxes of
 //     the model and the update is c += dt/dx^2 sum(F+ - F-);
-//   * FP32 reciprocals use the hardware approximation (a few ulp), FP64 is
-//     exact IEEE.
+//   * FP32 reciprocals and logarithms use the hardware approximations (a few
+//     ulp), FP64 is exact IEEE.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -59,7 +60,8 @@ __device__ __forceinline__ float2 vsub(float2 a, float2 b) {
     return r;
 }
 __device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
-__device__ __forceinline__ float2 vlog(float2 a) { return make_float2(logf(a.x), logf(a.y)); }
+// the hardware-approximated logarithm (a few ulp; the FP64 path is exact)
+__device__ __forceinline__ float2 vlog(float2 a) { return make_float2(__logf(a.x), __logf(a.y)); }
 __device__ __forceinline__ float2 vpair(float a, float b) { return make_float2(a, b); }
 
 __device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -103,23 +105,29 @@ struct PTile {
     using Q = Q2<V>;
     static constexpr int TYP = TY / 2;                  // pair rows
     static constexpr int NT = TX * TYP;                 // threads
-    static constexpr int HX = TX + 4, HYP = TYP + 2;    // halo-2 plane in pairs
-    static constexpr int HP = HX * HYP;
-    static constexpr int RX = TX + 2, RP = RX * HYP;    // halo-1 ring (all pair rows)
-    static constexpr int JH = (HP + NT - 1) / NT;
-    static constexpr int JR = (RP + NT - 1) / NT;
+    static constexpr int HW = TX + 4, HYP = TYP + 2;    // halo-2 plane: HW x HYP pair cells
+    static constexpr int NH = HW * HYP;
+    static constexpr int RW = TX + 2, NR = RW * HYP;    // halo-1 ring (all pair rows)
+    // Row pitch of the plane arrays (measured: an odd pitch TX + 5 and a
+    // 128-byte-aligned pitch TX + 8 were both slower than the dense TX + 4).
+    static constexpr int HX = HW, RX = HX;
+    static constexpr int OQ = 0, OV = 0, OD = 0, OF = 0;    // base shifts (elements)
+    static constexpr int HP = HX * HYP, RP = HP;            // plane stride
+    static constexpr int FXP = TX + 1;                      // x-face row pitch
+    static constexpr int NHP = (NH + 15) / 16 * 16;         // staging field stride (128-byte multiple)
+    static constexpr int JH = (NH + NT - 1) / NT;
     static constexpr size_t OFF_A = 0;                                   // {phi, Y}, 4 planes
     static constexpr size_t OFF_B = OFF_A + sizeof(Q) * 4 * HP;          // {mu_s, mu_l}, 4 planes
     static constexpr size_t OFF_C = OFF_B + sizeof(Q) * 4 * HP;          // {c_s, c_l}, 3 planes
     static constexpr size_t OFF_P = OFF_C + sizeof(Q) * 3 * HP;          // phi, 3 planes
     static constexpr size_t OFF_D = OFF_P + sizeof(V) * 3 * HP;          // dx^2 phidot, 2 planes
     static constexpr size_t OFF_FX = OFF_D + sizeof(V) * 2 * RP;         // x faces {F_c, F_d}
-    static constexpr size_t OFF_FY = OFF_FX + sizeof(Q) * TYP * (TX + 1);   // upper y face
-    static constexpr size_t OFF_R = OFF_FY + 2 * sizeof(T) * (TYP + 1) * TX;   // next plane: phi, c, d
-    static constexpr size_t OFF_O = OFF_R + sizeof(V) * 3 * HP;               // own c, d, c_lo
+    static constexpr size_t OFF_FY = OFF_FX + sizeof(Q) * (TYP * FXP);       // upper y face {F_c, F_d}
+    static constexpr size_t OFF_R = OFF_FY + sizeof(V) * (TYP + 1) * TX;     // next plane: phi, c, d
+    static constexpr size_t OFF_O = OFF_R + sizeof(V) * 3 * NHP;             // own c, d, c_lo
     static constexpr size_t BYTES = OFF_O + sizeof(V) * 3 * NT;
-    static constexpr int NB = RP - NT;   // ring cells besides the threads' own pairs
-    static_assert(NB == 2 * RX + 2 * TYP && NB <= NT, "ring = own pairs + border");
+    static constexpr int NB = NR - NT;   // ring cells besides the threads' own pairs
+    static_assert(NB == 2 * RW + 2 * TYP && NB <= NT, "ring = own pairs + border");
 };
 
 // asynchronous global -> shared copies (cp.async, completion awaited per thread)
@@ -209,16 +217,17 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     using V = typename L::V;
     using Q = typename L::Q;
     constexpr int HX = L::HX, HP = L::HP, RX = L::RX, RP = L::RP, NT = L::NT, TYP = L::TYP;
+    constexpr int HW = L::HW, NH = L::NH, NHP = L::NHP, RW = L::RW, FXP = L::FXP;
     static_assert(HP < 4096, "tile too large for the packed ring descriptors");
     static_assert(NT >= 32 + TX && TYP <= 32, "edge faces need warps 0 and 1");
     extern __shared__ __align__(16) unsigned char smem[];
-    Q* sA = reinterpret_cast<Q*>(smem + L::OFF_A);
-    Q* sB = reinterpret_cast<Q*>(smem + L::OFF_B);
-    Q* sC = reinterpret_cast<Q*>(smem + L::OFF_C);
-    V* sP = reinterpret_cast<V*>(smem + L::OFF_P);
-    V* sD = reinterpret_cast<V*>(smem + L::OFF_D);
-    Q* sFx = reinterpret_cast<Q*>(smem + L::OFF_FX);
-    T* sFy = reinterpret_cast<T*>(smem + L::OFF_FY);
+    Q* sA = reinterpret_cast<Q*>(smem + L::OFF_A) + L::OQ;
+    Q* sB = reinterpret_cast<Q*>(smem + L::OFF_B) + L::OQ;
+    Q* sC = reinterpret_cast<Q*>(smem + L::OFF_C) + L::OQ;
+    V* sP = reinterpret_cast<V*>(smem + L::OFF_P) + L::OV;
+    V* sD = reinterpret_cast<V*>(smem + L::OFF_D) + L::OD;
+    Q* sFx = reinterpret_cast<Q*>(smem + L::OFF_FX) + L::OF;
+    V* sFy = reinterpret_cast<V*>(smem + L::OFF_FY);
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -227,16 +236,20 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     const long long sz = (long long)nx * ny;
 
     // ---- work lists, fixed for the whole z-march
+    // halo pair cells this thread loads (staging index tid + j NT) and converts
+    // (ring index hring[j] in the pitched plane arrays)
     int hoff[L::JH][2];   // in-plane offsets of the two rows of each loaded pair cell, -1: ghost
+    int hring[L::JH];
 #pragma unroll
     for (int j = 0; j < L::JH; ++j) {
         const int h = tid + j * NT;
         hoff[j][0] = hoff[j][1] = -1;
-        if (h < HP) {
-            const int mx = map_coord(x0 - 2 + h % HX, nx, G.bc_lo[0], G.bc_hi[0]);
+        hring[j] = (h / HW) * HX + h % HW;
+        if (h < NH) {
+            const int mx = map_coord(x0 - 2 + h % HW, nx, G.bc_lo[0], G.bc_hi[0]);
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                const int my = map_coord(y0 - 2 + 2 * (h / HX) + l, ny, G.bc_lo[1], G.bc_hi[1]);
+                const int my = map_coord(y0 - 2 + 2 * (h / HW) + l, ny, G.bc_lo[1], G.bc_hi[1]);
                 if (mx >= 0 && my >= 0) hoff[j][l] = my * nx + mx;
             }
         }
@@ -259,10 +272,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     if (tid >= NT - NB) {
         const int b = tid - (NT - NB);
         int rx, ry;
-        if (b < RX) { rx = b; ry = 0; }
-        else if (b < 2 * RX) { rx = b - RX; ry = L::HYP - 1; }
-        else if (b < 2 * RX + TYP) { rx = 0; ry = 1 + b - 2 * RX; }
-        else { rx = RX - 1; ry = 1 + b - 2 * RX - TYP; }
+        if (b < RW) { rx = b; ry = 0; }
+        else if (b < 2 * RW) { rx = b - RW; ry = L::HYP - 1; }
+        else if (b < 2 * RW + TYP) { rx = 0; ry = 1 + b - 2 * RW; }
+        else { rx = RW - 1; ry = 1 + b - 2 * RW - TYP; }
         ring_desc(rx, ry, bor_dsc, bor_xc);
         bor_r = ry * RX + rx;
     }
@@ -287,19 +300,19 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 #pragma unroll
         for (int j = 0; j < L::JH; ++j) {
             const int h = tid + j * NT;
-            if ((j + 1) * NT > HP && h >= HP) break;
+            if ((j + 1) * NT > NH && h >= NH) break;
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 T* dst = sR + 2 * h + l;
                 if (mz >= 0 && hoff[j][l] >= 0) {
                     const long long gi = (long long)mz * sz + hoff[j][l];
                     cp_async(dst, phi_in + gi);
-                    cp_async(dst + 2 * HP, c_in + gi);
-                    cp_async(dst + 4 * HP, d_in + gi);
+                    cp_async(dst + 2 * NHP, c_in + gi);
+                    cp_async(dst + 4 * NHP, d_in + gi);
                 } else {
                     dst[0] = G.dir_phi;
-                    dst[2 * HP] = G.dir_c;
-                    dst[4 * HP] = G.dir_d;
+                    dst[2 * NHP] = G.dir_c;
+                    dst[4 * NHP] = G.dir_d;
                 }
             }
         }
@@ -327,9 +340,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V* R = reinterpret_cast<const V*>(sR);
 #pragma unroll
         for (int j = 0; j < L::JH; ++j) {
-            const int h = tid + j * NT;
-            if ((j + 1) * NT > HP && h >= HP) break;
-            const V f = R[h], c = R[HP + h], d = R[2 * HP + h];
+            const int hl = tid + j * NT;
+            if ((j + 1) * NT > NH && hl >= NH) break;
+            const V f = R[hl], c = R[NHP + hl], d = R[2 * NHP + hl];
+            const int h = hring[j];
             const V p = vp_of(K, f);
             const V cs = vfma(vsub(K.one, p), d, c);
             const V cl = vsub(c, vmul(p, d));
@@ -558,8 +572,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     V fxc, fxd, fyc, fyd, fzc, fzd;
     // update of plane k from its fluxes and the own-cell state staged in sO
     auto update = [&](int k) {
-        const Q left = sFx[ty * (TX + 1) + tx];
-        const T bc_ = sFy[2 * (ty * TX + tx)], bd_ = sFy[2 * (ty * TX + tx) + 1];
+        const Q left = sFx[ty * FXP + tx];
+        const V below = sFy[ty * TX + tx];
+        const T bc_ = below.x, bd_ = below.y;
         const V dFc = vadd(vadd(vsub(fxc, left.a), vpair(fyc.x - bc_, fyc.y - fyc.x)), vsub(fzc, fzc_down));
         const V dFd = vadd(vadd(vsub(fxd, left.b), vpair(fyd.x - bd_, fyd.y - fyd.x)), vsub(fzd, fzd_down));
         const V* O = reinterpret_cast<const V*>(sO);
@@ -618,22 +633,20 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         fyc = vmask(fyc, nf_ylo, nf_yhi);
         fyd = vmask(fyd, nf_ylo, nf_yhi);
         if (z_noflux(k)) fzc = fzd = vpair(T(0), T(0));
-        sFx[ty * (TX + 1) + tx + 1] = Q{fxc, fxd};
-        sFy[2 * ((ty + 1) * TX + tx)] = fyc.y;
-        sFy[2 * ((ty + 1) * TX + tx) + 1] = fyd.y;
+        sFx[ty * FXP + tx + 1] = Q{fxc, fxd};
+        sFy[(ty + 1) * TX + tx] = vpair(fyc.y, fyd.y);
         if (tid < TYP) {
             // x faces on the tile's low x edge, pair row tid
             V ec, ed;
             xface(k, (tid + 1) * HX + 1, (tid + 1) * RX, ec, ed);
             if (nf_x_edge) ec = ed = vpair(T(0), T(0));
-            sFx[tid * (TX + 1)] = Q{ec, ed};
+            sFx[tid * FXP] = Q{ec, ed};
         } else if (tid >= 32 && tid < 32 + TX) {
             // y face on the tile's low y edge (upper lane of the pair row below the tile)
             const int ex = tid - 32;
             V ec, ed;
             yface(k, ex + 2, ex + 1, ec, ed);
-            sFy[2 * ex] = nf_y_edge ? T(0) : ec.y;
-            sFy[2 * ex + 1] = nf_y_edge ? T(0) : ed.y;
+            sFy[ex] = nf_y_edge ? vpair(T(0), T(0)) : vpair(ec.y, ed.y);
         }
         __syncthreads();
     }

@@ -401,6 +401,42 @@ def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, it
     return {w: cur[w] for w in wrt}, hist
 
 
+class KvProblem:
+    """The fixed part of a k(V) calibration problem for kv_loss: instances,
+    initial fields, step count, targets, precision."""
+
+    def __init__(self, pr, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, precision="fp32", dt=None):
+        self.pr, self.lengths, self.v_pull = dict(pr), lengths, v_pull
+        self.fields = (phi0, cs0, cl0)
+        self.nsteps, self.k_target, self.precision, self.dt = nsteps, k_target, precision, dt
+
+    def run(self, theta):
+        pr = dict(self.pr, **{n: float(t) for n, t in zip(ADJ_PARAMS, theta)})
+        return adjoint(pr, self.lengths, self.v_pull, *self.fields, self.nsteps, k_target=self.k_target,
+                       precision=self.precision, dt=self.dt)
+
+
+def kv_loss(theta, problem: KvProblem):
+    """sum_i (k_i - k_target_i)^2 as a differentiable torch scalar of
+    theta = (M_phi, A, b) (a float64 tensor of 3): forward and the derivatives
+    come from one pf_adjoint run; backward scales the stored gradient."""
+    import torch
+
+    class _KvLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            r = problem.run(th.detach().cpu().numpy())
+            ctx.save_for_backward(torch.as_tensor(r["grad"], dtype=th.dtype, device=th.device))
+            return torch.as_tensor(r["loss"], dtype=th.dtype, device=th.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad
+
+    return _KvLoss.apply(theta)
+
+
 def energy_solute_noalloc(pr: dict, phi, cs, cl, out, precision="fp32", step=0, shifts=0, stream=None):
     """pf_energy_solute_noalloc on CUDA tensors: writes (F_h, S_h) into the
     2-element float64 CUDA tensor `out` without allocating device memory."""

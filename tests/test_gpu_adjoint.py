@@ -144,3 +144,31 @@ def test_adam_calibration_lowers_the_loss():
                                wrt=("A",), precision="fp64", dt=dts)
     assert hist[-1] < 0.2 * hist[0], hist
     assert abs(theta["A"] - 1.15) < abs(1.05 - 1.15)
+
+
+def test_torch_autograd_loss():
+    """kv_loss as a torch.autograd function: its gradient is pf_adjoint's, and
+    torch's own Adam on it lowers the loss."""
+    torch = pytest.importorskip("torch")
+    lengths, vs = [160, 200], [0.1, 0.3]
+    prs, dts, phi, cs, cl = inputs(lengths, vs, A=1.15)
+    kt = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 300, precision="fp64", dt=dts)["k"]
+    prob = pf.KvProblem(dict(prs[0], A=1.05), lengths, vs, phi, cs, cl, 300, kt, precision="fp64", dt=dts)
+    th = torch.tensor([prs[0]["M_phi"], 1.05, prs[0]["b"]], dtype=torch.float64, requires_grad=True)
+    loss = pf.kv_loss(th, prob)
+    loss.backward()
+    ref = prob.run(th.detach().numpy())
+    assert float(loss.detach()) == pytest.approx(ref["loss"], rel=1e-15)
+    np.testing.assert_allclose(th.grad.numpy(), ref["grad"], rtol=1e-15, atol=0)
+    a = torch.tensor([1.05], dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([a], lr=0.02)
+    fixed = torch.tensor([prs[0]["M_phi"], prs[0]["b"]], dtype=torch.float64)
+    losses = []
+    for _ in range(10):
+        opt.zero_grad()
+        l = pf.kv_loss(torch.cat([fixed[:1], a, fixed[1:]]), prob)
+        l.backward()
+        opt.step()
+        losses.append(float(l.detach()))
+    assert losses[-1] < 0.2 * losses[0], losses
+

@@ -164,15 +164,16 @@ def total_c(pr, phi, cs, cl):
     return p, p * cs + (1 - p) * cl
 
 
-def check_fp32(pr, st, g, S0g, S1g, tol_c=1e-5):
+def check_fp32(pr, st, g, S0g, S1g, tol_c=1e-5, tol_phi=1e-4, tol_phase=1e-4):
     gphi, gcs, gcl = (a.astype(np.float64) for a in g)
-    assert np.abs(gphi - st.phi).max() <= 1e-4
+    assert np.abs(gphi - st.phi).max() <= tol_phi, np.abs(gphi - st.phi).max()
     po, co = total_c(pr, st.phi, st.cs, st.cl)
     _, cg = total_c(pr, gphi, gcs, gcl)
     assert rel_err(cg, co) <= tol_c, f"total c: {rel_err(cg, co):.2e}"
     sol, liq = po >= 0.5, po <= 0.5
-    assert np.abs(gcs - st.cs)[sol].max() <= 1e-4 * np.abs(st.cs[sol]).max()
-    assert np.abs(gcl - st.cl)[liq].max() <= 1e-4 * np.abs(st.cl[liq]).max()
+    assert sol.any() and liq.any(), "no interface left to compare"
+    assert np.abs(gcs - st.cs)[sol].max() <= tol_phase * np.abs(st.cs[sol]).max()
+    assert np.abs(gcl - st.cl)[liq].max() <= tol_phase * np.abs(st.cl[liq]).max()
     assert abs(S1g - S0g) <= 1e-7 * abs(S0g)
 
 
@@ -204,3 +205,27 @@ def test_fp32_2d_perturbed_1e4_steps():
         g = s.get_fields()
         S1g = s.solute_total()
     check_fp32(pr, st, g, S0g, S1g)
+
+
+def test_fp32_3d_sphere_3000_steps():
+    """The 3D FP32 step (two-lane packed arithmetic, approximate reciprocals and
+    logarithms) on a growing sphere seed over a ragged 70 x 38 x 33 grid: same
+    bars as the 1D/2D FP32 runs except phi.  At undercooling 0.2 the solid
+    fraction grows from 8 % to 89 % in the 3000 steps; the front travels ~20
+    cells and its FP32 position drifts by ~4e-4 cells, which through the
+    interface slope of ~0.35 per cell puts 1.4e-4 on phi (measured, the same
+    with exact or hardware logarithms) and 1.6e-4 on the phase concentrations
+    next to the front, so these are held at 2.5e-4 here; the total c stays at
+    1e-5 (measured 1.1e-6)."""
+    pr, phi, cs, cl = wl.sphere_seed_3d(n=(70, 38, 33), radius_cells=12.0, u=0.2, A=1.0, b=1.0)
+    phi, cs, cl = (np.asarray(a, np.float32).astype(np.float64) for a in (phi, cs, cl))
+    st = oracle.State(pr, phi, cs, cl)
+    st.step(3000)
+    with Sim(pr, "fp32") as s:
+        s.set_fields(phi, cs, cl)
+        S0g = s.solute_total()
+        s.step(3000)
+        g = s.get_fields()
+        S1g = s.solute_total()
+    check_fp32(pr, st, g, S0g, S1g, tol_phi=2.5e-4, tol_phase=2.5e-4)
+
