@@ -88,6 +88,21 @@ def step3d_traffic(cells):
     return TRAFFIC_CAPTURE["bytes_per_cell_update"] * cells
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job's time); the identity without a process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def weak_scaling_rate(cells_per_rank, steps, world, seconds):
+    """Whole-job cell-updates per second: every rank advances its own grid."""
+    return cells_per_rank * steps * world / seconds
+
+
 def load_peaks():
     """(HBM GB/s, SM max MHz, source) from MEASURED_PEAKS.json, else the fallback."""
     try:
@@ -450,12 +465,9 @@ def main():
         e2e_s = time.perf_counter() - t0
         sim.close()
 
-    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = float(t[0]), float(t[1])
-    value = cells * args.steps * world / (ms_max * 1e-3)
-    e2e_value = cells * ke * world / e2e_max
+    ms_max, e2e_max = max_over_ranks([ms, e2e_s], dist, device="cuda")
+    value = weak_scaling_rate(cells, args.steps, world, ms_max * 1e-3)
+    e2e_value = weak_scaling_rate(cells, ke, world, e2e_max)
 
     if rank == 0:
         hbm_peak, sm_mhz, how = load_peaks()

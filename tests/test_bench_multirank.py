@@ -1,0 +1,48 @@
+"""bench.py's multi-rank bookkeeping (the N > 1 path) on two gloo ranks on
+the CPU: the job time is the slowest rank's, and the weak-scaling rate counts
+every rank's cells."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local = [10.0 + 5.0 * rank, 2.0 - rank]        # ms of the timed steps, e2e seconds
+    ms, e2e = bench.max_over_ranks(local, dist)
+    out[rank] = (ms, e2e, bench.weak_scaling_rate(1000, 20, world, ms * 1e-3))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time():
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    for rank in (0, 1):
+        ms, e2e, rate = res[rank]
+        assert ms == 15.0 and e2e == 2.0
+        assert rate == pytest.approx(1000 * 20 * 2 / 15e-3)
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks([3.0, 4.0]) == [3.0, 4.0]
