@@ -65,10 +65,10 @@ SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 # sources the capture ran.  The figure is reported as null as soon as those
 # sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.422400e6 + 229.353472e6) / 256 ** 3,
+    "bytes_per_cell_update": (280.906240e6 + 231.764736e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_internal.cuh", "pf_kernels.h"),
-    "sha256": ("f795c54d9ceee6349b22091fb4e0054f4bdb7039194f554652b2c673283a7c4e",
+    "sha256": ("53e33495cc7b54d68da158dda0f60419b649bc1323daf1c3635d2eaa0befe389",
                "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60",
                "6f2b278b5cc421adbf544bb59fc1386d67b011600adc02e65bcfb5f7ad7347a0"),
 }

@@ -122,9 +122,11 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
 
 /* Copy the three fields in (pf_set_fields) or out (pf_get_fields).  Each
  * pointer addresses n[0]*n[1]*n[2] values of the handle's precision (float or
- * double), x fastest; where = PF_HOST (any host memory; pinned memory makes the
- * copy asynchronous-capable) or PF_DEVICE.  pf_get_fields synchronises the
- * stream. */
+ * double), x fastest; where = PF_HOST (any host memory) or PF_DEVICE.  With
+ * PF_HOST, pf_set_fields reads page-locked (pinned or registered) host memory
+ * directly from the conversion kernel and stages other host memory through a
+ * device copy; both synchronise the stream before returning, so the caller may
+ * reuse its buffers at once.  pf_get_fields synchronises the stream. */
 int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where);
 int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
 

@@ -204,7 +204,28 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     const size_t bytes = (size_t)h->P.cells() * h->P.elem();
     const void* src[3] = {phi, cs, cl};
+    bool mapped = where == PF_HOST;
     if (where == PF_HOST) {
+        // page-locked host memory is readable by the conversion kernel itself
+        // (over NVLink-C2C / PCIe): convert straight from it, without staging
+        for (int f = 0; f < 3 && mapped; ++f) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, src[f]) != cudaSuccess) {
+                cudaGetLastError();
+                mapped = false;
+            } else if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) {
+                mapped = false;
+            } else {
+                src[f] = at.devicePointer;
+            }
+        }
+        if (!mapped) {
+            src[0] = phi;
+            src[1] = cs;
+            src[2] = cl;
+        }
+    }
+    if (where == PF_HOST && !mapped) {
         // stage (phi, c_s, c_l) in the idle ping-pong buffer, then convert
         const pf::Fields& st = h->buf[h->cur ^ 1];
         void* dst[3] = {st.phi, st.c, st.d};
@@ -218,7 +239,7 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
     if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
     h->have_front = false;
     if (where == PF_HOST) {
-        // the caller may reuse pageable host memory as soon as we return
+        // the caller may reuse its host memory as soon as we return
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     }

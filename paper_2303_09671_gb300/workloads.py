@@ -242,3 +242,40 @@ def pulled_front_1d(N=1024, dx=0.5, k_e=0.1, D_s=1e-4, V=0.1, G_theta=5.25e-3, f
     cs = np.full(N, k_e * pr["c_inf"])
     cl = np.full(N, pr["c_inf"])
     return pr, phi, cs, cl
+
+
+# ---------------------------------------------------------- physical units
+# Table 1 of the paper (atomic per cent; SI otherwise): equilibrium partition
+# coefficient, melting point [K], liquidus slope [K/%], alloy concentration
+# [%], Gibbs-Thomson coefficient [K m], capillary length [m], liquid
+# diffusivity [m^2/s], kinetic coefficient [s/m].
+ALLOYS = {
+    "Si-As": dict(k_e=0.3, T_m=1685.0, m=-4.0, c_inf=9.0, Gamma=3.4e-7, d0=13.5e-9, D_l=15e-9, beta=0.595),
+    "Ni-Cu": dict(k_e=0.5, T_m=1728.0, m=-2.0, c_inf=5.0, Gamma=2.6e-7, d0=26e-9, D_l=3e-9, beta=0.2),
+}
+
+
+def physical_units(alloy, W=None):
+    """Scales of the library's units for an alloy of Table 1: length W (default
+    d_0, i.e. eps = W/d_0 = 1), time W^2/D_l, concentration c_inf, temperature
+    |m| c_inf (theta = (T_m - T) / (|m| c_inf))."""
+    a = ALLOYS[alloy]
+    W = a["d0"] if W is None else float(W)
+    return dict(length_m=W, time_s=W * W / a["D_l"], conc=a["c_inf"], temp_K=abs(a["m"]) * a["c_inf"],
+                eps=W / a["d0"])
+
+
+def physical_pulled_front(alloy, v_p, G, Ds_ratio, *, N=2048, dx=0.5, W=None, front_cell=None, **kw):
+    """A pulled 1D front of a Table 1 alloy: pulling speed v_p [m/s], frozen
+    gradient G [K/m], D_s/D_l, interface width W [m] (default d_0), converted to
+    scaled units (V = v_p W / D_l, G_theta = G W / (|m| c_inf)); the start is that
+    of pulled_front_1d (interface at the solidus of c_inf)."""
+    a = ALLOYS[alloy]
+    u = physical_units(alloy, W)
+    V = v_p * u["length_m"] / a["D_l"]
+    G_theta = G * u["length_m"] / u["temp_K"]
+    pr, phi, cs, cl = pulled_front_1d(N=N, dx=dx, k_e=a["k_e"], D_s=Ds_ratio, V=V, G_theta=G_theta,
+                                      front_cell=front_cell, eps=u["eps"], **kw)
+    pr["units"] = u
+    return pr, phi, cs, cl
+
