@@ -65,12 +65,12 @@ SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 # sources the capture ran.  The figure is reported as null as soon as those
 # sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.906240e6 + 231.764736e6) / 256 ** 3,
+    "bytes_per_cell_update": (280.811776e6 + 231.734272e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_internal.cuh", "pf_kernels.h"),
-    "sha256": ("53e33495cc7b54d68da158dda0f60419b649bc1323daf1c3635d2eaa0befe389",
+    "sha256": ("33e195e8a4e3313311c95a41d7daee8e0a52812efeee407fa26315e6d8fa3ddc",
                "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60",
-               "6f2b278b5cc421adbf544bb59fc1386d67b011600adc02e65bcfb5f7ad7347a0"),
+               "0f6e6d54b674f78de937e97d1348d41647f83bf53000b0ae9aec76ea7aca0a15"),
 }
 
 

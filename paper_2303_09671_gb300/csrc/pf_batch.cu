@@ -352,22 +352,25 @@ cudaError_t raise_smem(K kern, int optin) {
 
 template <typename T>
 cudaError_t set_smem_limits(size_t* max_dynamic) {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    static size_t limit = 0;
-    std::call_once(once, [] {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    static DeviceSetup setup;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(setup.mu);
+    if (!setup.done[dev]) {
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 128>, optin);
         if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 256>, optin);
         if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 512>, optin);
         if (e == cudaSuccess) e = raise_smem(batch_kernel<T, 1024>, optin);
-        limit = (size_t)optin - 1024;   // static part: reduction scratch and flag
-        err = e;
-    });
-    *max_dynamic = limit;
-    return err;
+        setup.value[dev] = (size_t)optin - 1024;   // static part: reduction scratch and flag
+        setup.err[dev] = e;
+        setup.done[dev] = true;
+    }
+    *max_dynamic = setup.value[dev];
+    return setup.err[dev];
 }
 
 struct Group {

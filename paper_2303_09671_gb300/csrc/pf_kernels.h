@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <cuda_runtime.h>
 
@@ -60,6 +61,19 @@ cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& o
 cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* cs, const void* cl,
                             const Fields& out, cudaStream_t s);
 void set_create_error(const std::string& msg);
+
+// One-time set-up of a kernel's launch attributes, per device: function
+// attributes such as the dynamic shared-memory limit belong to the device the
+// kernel is configured on, so a process that uses several GPUs configures each.
+struct DeviceSetup {
+    static constexpr int MAX_DEVICES = 64;
+    std::mutex mu;
+    bool done[MAX_DEVICES] = {};
+    int per_sm[MAX_DEVICES] = {};
+    int sms[MAX_DEVICES] = {};
+    size_t value[MAX_DEVICES] = {};
+    cudaError_t err[MAX_DEVICES] = {};
+};
 
 cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
                               cudaStream_t s);

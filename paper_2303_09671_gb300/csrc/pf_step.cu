@@ -431,18 +431,25 @@ template <typename T, int DIM, int TX, int TY>
 static cudaError_t launch_tile(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K) {
     using L = Tile<T, DIM, TX, TY>;
     auto kern = step_kernel<T, DIM, TX, TY>;
-    static bool configured = false;
-    static int per_sm = 1, sms = 1;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L::BYTES);
+    static DeviceSetup setup;
+    int dev = 0, per_sm = 1, sms = 1;
+    {
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * L::TYe, L::BYTES);
-        if (per_sm < 1) per_sm = 1;
-        configured = true;
+        if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(setup.mu);
+        if (!setup.done[dev]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+            if (e != cudaSuccess) return e;
+            int s = 1, p = 1;
+            cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kern, TX * L::TYe, L::BYTES);
+            setup.sms[dev] = s;
+            setup.per_sm[dev] = p < 1 ? 1 : p;
+            setup.done[dev] = true;
+        }
+        per_sm = setup.per_sm[dev];
+        sms = setup.sms[dev];
     }
     dim3 block(TX * L::TYe);
     dim3 grid((C.n[0] + TX - 1) / TX, (DIM >= 2) ? (C.n[1] + TY - 1) / TY : 1, 1);

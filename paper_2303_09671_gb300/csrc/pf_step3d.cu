@@ -733,18 +733,26 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     using L = PTile<T, TX, TY>;
     auto k19 = step3d_kernel<T, TX, TY, true>;
     auto k7 = step3d_kernel<T, TX, TY, false>;
-    static bool configured = false;
-    static int per_sm = 1, sms = 1;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k19, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    static DeviceSetup setup;
+    int dev = 0, per_sm = 1, sms = 1;
+    {
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k19, L::NT, L::BYTES);
-        if (per_sm < 1) per_sm = 1;
-        configured = true;
+        if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(setup.mu);
+        if (!setup.done[dev]) {
+            e = cudaFuncSetAttribute(k19, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+            if (e != cudaSuccess) return e;
+            int s = 1, p = 1;
+            cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k19, L::NT, L::BYTES);
+            setup.sms[dev] = s;
+            setup.per_sm[dev] = p < 1 ? 1 : p;
+            setup.done[dev] = true;
+        }
+        per_sm = setup.per_sm[dev];
+        sms = setup.sms[dev];
     }
     const HostProblem& P = *a.prob;
     const PairConsts<typename L::V> K = make_pair_consts<T>(P, C);
