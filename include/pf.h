@@ -188,7 +188,10 @@ typedef struct {
     const void* cs0;       /* host memory, element type of params.precision        */
     const void* cl0;
     double dx;
-    pf_bc bc;              /* lo[0] must be PF_BC_NOFLUX, hi[0] PF_BC_DIRICHLET */
+    pf_bc bc;              /* lo[0] must be PF_BC_NOFLUX; hi[0] PF_BC_DIRICHLET, or
+                              PF_BC_NOFLUX for closed boxes without a moving window
+                              (all v_pull = 0), e.g. the planar front of Sec.
+                              "Numerical technique" with F_h recorded every step */
     pf_params params;
     int64_t max_steps;         /* per instance */
     int64_t steps_per_launch;  /* steps of one persistent launch (> 0) */
@@ -199,6 +202,9 @@ typedef struct {
     double min_travel;         /* ... and the temperature has been pulled >= min_travel
                                   (units of W), i.e. t >= min_travel / v */
     int cells_per_thread;      /* 1, 2, 4 or 8; 0 = autotune */
+    int64_t energy_every;      /* > 0: record the free energy F_h (as pf_energy
+                                  computes it) after every energy_every-th step,
+                                  in FP64 inside the persistent launch; 0: none */
 } pf_batch_desc;
 
 typedef struct {
@@ -213,6 +219,9 @@ typedef struct {
     int cells_per_thread;  /* the value used (autotuned or given) */
     int64_t launches;      /* batch-kernel launches issued */
     double gpu_ms;         /* device time of the stepping (CUDA events) */
+    double* energy;        /* optional (may be NULL), with energy_every > 0: host
+                              array [n_instances][max_steps / energy_every] of F_h
+                              records; NaN where an instance had stopped */
 } pf_batch_result;
 
 /* Run the batch until every instance has converged or taken max_steps

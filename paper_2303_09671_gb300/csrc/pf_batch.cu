@@ -58,6 +58,11 @@ struct BatchArgs {
     double theta_ref, G_theta, x0, c_inf;
     T gphi, gcs, gcl, gmus, gmul;   // Dirichlet (hot end) ghost
     T fc, fd;                       // fresh-layer state of the moving window
+    int hot_noflux;                 // 1: mirror ghost and zero flux at the hot end too
+    long long energy_every;         // record F_h every this many steps (0: never)
+    int energy_slots;               // records per instance in `energy`
+    double* energy;                 // [instance][slot] F_h records (device)
+    double dir_phi;                 // hot-end ghost phi, for the gradient energy
 };
 
 template <typename T>
@@ -138,15 +143,18 @@ batch_kernel(BatchArgs<T> a) {
             sMl[i] = flog(cl);
         }
         __syncthreads();
-        // P2: phase-field rate (cold end: mirror ghost; hot end: Dirichlet ghost)
+        // P2: phase-field rate (cold end: mirror ghost; hot end: Dirichlet or
+        // mirror ghost)
         for (int i = tid; i < n; i += NT) {
             const int im = (i == 0) ? 0 : i - 1;
+            const bool last = i == n - 1, mirror_hot = last && a.hot_noflux;
+            const int ip = last ? i : i + 1;
             const T fc = sPhi[i];
             const T fW = sPhi[im];
-            const T fE = (i == n - 1) ? a.gphi : sPhi[i + 1];
+            const T fE = (last && !mirror_hot) ? a.gphi : sPhi[ip];
             const T mW_s = sMs[im], mW_l = sMl[im];
-            const T mE_s = (i == n - 1) ? a.gmus : sMs[i + 1];
-            const T mE_l = (i == n - 1) ? a.gmul : sMl[i + 1];
+            const T mE_s = (last && !mirror_hot) ? a.gmus : sMs[ip];
+            const T mE_l = (last && !mirror_hot) ? a.gmul : sMl[ip];
             T p, cs, cl;
             cs_cl(i, p, cs, cl);
             const T mus = sMs[i], mul = sMl[i];
@@ -198,6 +206,9 @@ batch_kernel(BatchArgs<T> a) {
                 const T YR = mlR + pR * (msR - mlR);
                 face1(C, f0, fR, cs0, csR, cl0, clR, pd0, sPd[i + 1], (fR - f0) * C.inv_dx,
                       (YR - Y0) * C.inv_dx, (msR - ms0) * C.inv_dx, (mlR - ml0) * C.inv_dx, FcR, FdR);
+            } else if (a.hot_noflux) {   // closed hot end: no flux through the last face
+                FcR = T(0);
+                FdR = T(0);
             } else {       // face to the fixed hot-end ghost (phase-field rate 0)
                 const T gp = p_of(C, a.gphi);
                 const T YR = a.gmul + gp * (a.gmus - a.gmul);
@@ -242,6 +253,45 @@ batch_kernel(BatchArgs<T> a) {
             shifts += 1;
         }
         __syncthreads();
+        // F_h of the new state (the discrete free energy of pf_energy), FP64
+        if (a.energy_every > 0 && (step % a.energy_every) == 0) {
+            const double t = (double)step * a.dt[inst];
+            const double th0 = a.theta_ref + a.G_theta * (a.x0 + v * t - (double)shifts * (double)C.dx);
+            const double dxd = (double)C.dx, ke = (double)C.one_m_ke;
+            double e = 0.0;
+            for (int i = tid; i < n; i += NT) {
+                const double f = (double)sPhi[i], cc = (double)sC[i], dd = (double)sD[i];
+                const double g = f * (1.0 - f);
+                const double h = f * f * ((double)C.h2 + f * ((double)C.h3 + f * ((double)C.h4 + f * (double)C.h5)));
+                const double p = h + (double)C.a * (f - 0.5) * g * g;
+                const double cs = cc + (1.0 - p) * dd, cl = cc - p * dd;
+                const double th = th0 - (double)C.G_theta * (((double)i + 0.5) * dxd);
+                const double fs = -ke * th + cs * (log(cs) - (double)C.log_ke - 1.0);
+                const double fl = cl * (log(cl) - 1.0);
+                // gradient energy: each pair of cells once, from its left cell;
+                // mirror ghosts add nothing and the pair with a Dirichlet ghost
+                // counts half, as in pf_energy
+                double gs = 0.0;
+                if (i < n - 1) {
+                    const double dphi = (double)sPhi[i + 1] - f;
+                    gs = dphi * dphi;
+                } else if (!a.hot_noflux) {
+                    const double dphi = a.dir_phi - f;
+                    gs = 0.5 * dphi * dphi;
+                }
+                e += (double)C.H * g * g + p * fs + (1.0 - p) * fl + 0.5 * (double)C.sigma * gs / (dxd * dxd);
+            }
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if ((tid & 31) == 0) red[tid >> 5] = e;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < NT / 32; ++w) tot += red[w];
+                const long long slot = step / a.energy_every - 1;
+                if (slot < a.energy_slots) a.energy[(long long)inst * a.energy_slots + slot] = tot * dxd;
+            }
+            __syncthreads();
+        }
         // steady-state check on k_v = c_inf / c_max
         if (a.check_every > 0 && (step % a.check_every) == 0) {
             double cm = -1e300;
@@ -396,6 +446,8 @@ struct BatchRun {
     double *dv = nullptr, *ddt = nullptr;
     std::vector<Group> groups;
     std::vector<int> rep_dir;   // tangent runs: seeded parameter of each instance
+    double* energy = nullptr;   // F_h records [instance][slot] (device), or null
+    int energy_slots = 0;
     cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
     int64_t launches = 0;
 
@@ -406,7 +458,7 @@ struct BatchRun {
             if (g.stream) cudaStreamDestroy(g.stream);
             if (g.done) cudaEventDestroy(g.done);
         }
-        void* ptrs[] = {phi, c, d, st, dv, ddt};
+        void* ptrs[] = {phi, c, d, st, dv, ddt, energy};
         for (void* p : ptrs)
             if (p) cudaFree(p);
         if (fork) cudaEventDestroy(fork);
@@ -439,6 +491,11 @@ struct BatchRun {
         const double pg = p_of_host(P, D.bc.dir_phi);
         a.fc = T(pg * D.bc.dir_cs + (1.0 - pg) * D.bc.dir_cl);
         a.fd = T(D.bc.dir_cs - D.bc.dir_cl);
+        a.hot_noflux = D.bc.hi[0] == PF_BC_NOFLUX;
+        a.energy_every = D.energy_every;
+        a.energy_slots = energy_slots;
+        a.energy = energy;
+        a.dir_phi = D.bc.dir_phi;
         if constexpr (IsDual<T>::value) {
             // seed d/dtheta = 1 on the parameter of this group
             using VT = decltype(C.A.v);
@@ -535,6 +592,13 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
     if (e == cudaSuccess) e = cudaMalloc(&B.st, N * sizeof(BatchState));
     if (e == cudaSuccess) e = cudaMalloc(&B.dv, N * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&B.ddt, N * sizeof(double));
+    if (e == cudaSuccess && D.energy_every > 0) {
+        // one record per energy_every steps up to max_steps, NaN where never written
+        const int64_t slots = D.max_steps / D.energy_every;
+        B.energy_slots = (int)slots;
+        e = cudaMalloc(&B.energy, (size_t)N * slots * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.energy, 0xff, (size_t)N * slots * sizeof(double), main);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         err = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -686,6 +750,15 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
     R->cells_per_thread = cpt;
     R->launches = B.launches;
     R->gpu_ms = total_ms;
+    if (R->energy && B.energy) {
+        e = cudaMemcpyAsync(R->energy, B.energy, (size_t)N * B.energy_slots * sizeof(double),
+                            cudaMemcpyDeviceToHost, main);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+        if (e != cudaSuccess) {
+            err = std::string("batch energy records: ") + cudaGetErrorString(e);
+            return PF_ECUDA;
+        }
+    }
     if (R->phi && R->cs && R->cl) {
         T *ocs = nullptr, *ocl = nullptr;
         e = cudaMalloc(&ocs, fb);
@@ -754,9 +827,17 @@ int run_batch(const pf_batch_desc* D, pf_batch_result* R, void* stream, std::str
         return PF_EINVAL;
     }
     if (P.precision != PF_FP32 && P.precision != PF_FP64) { err = "precision must be PF_FP32 or PF_FP64"; return PF_EINVAL; }
-    if (D->bc.lo[0] != PF_BC_NOFLUX || D->bc.hi[0] != PF_BC_DIRICHLET) {
-        err = "batch instances need a no-flux cold end and a Dirichlet hot end";
+    if (D->bc.lo[0] != PF_BC_NOFLUX || (D->bc.hi[0] != PF_BC_DIRICHLET && D->bc.hi[0] != PF_BC_NOFLUX)) {
+        err = "batch instances need a no-flux cold end and a Dirichlet or no-flux hot end";
         return PF_EINVAL;
+    }
+    if (D->energy_every < 0 || (D->energy_every > 0 && D->max_steps / D->energy_every > (int64_t)1 << 26)) {
+        err = "energy_every must be 0 or leave at most 2^26 records per instance";
+        return PF_EINVAL;
+    }
+    if (D->bc.hi[0] == PF_BC_NOFLUX) {
+        for (int i = 0; i < D->n_instances; ++i)
+            if (D->v_pull[i] != 0.0) { err = "a moving window needs the Dirichlet hot end"; return PF_EINVAL; }
     }
     if (!(D->bc.dir_cs > 0) || !(D->bc.dir_cl > 0)) { err = "Dirichlet concentrations must be positive"; return PF_EINVAL; }
     if (D->steps_per_launch <= 0 || D->launches_per_graph <= 0 || D->check_every <= 0 || D->max_steps <= 0 ||
@@ -862,6 +943,7 @@ static int run_adjoint_T(const pf_adjoint_desc& A, pf_adjoint_result* R, cudaStr
     RD.v_pull = rv.data();
     RD.dt = rdt.data();
     RD.check_every = 0;   // fixed number of steps, no convergence test
+    RD.energy_every = 0;
     BatchRun<T> B(RD, main, err);
     B.rep_dir = rdir;
     B.off.resize(M);

@@ -57,7 +57,7 @@ class pf_batch_desc(ctypes.Structure):
                 ("max_steps", ctypes.c_int64), ("steps_per_launch", ctypes.c_int64),
                 ("launches_per_graph", ctypes.c_int), ("check_every", ctypes.c_int64),
                 ("window", ctypes.c_double), ("tol", ctypes.c_double), ("min_travel", ctypes.c_double),
-                ("cells_per_thread", ctypes.c_int)]
+                ("cells_per_thread", ctypes.c_int), ("energy_every", ctypes.c_int64)]
 
 
 class pf_batch_result(ctypes.Structure):
@@ -65,7 +65,8 @@ class pf_batch_result(ctypes.Structure):
                 ("t", ctypes.POINTER(ctypes.c_double)), ("steps", ctypes.POINTER(ctypes.c_int64)),
                 ("converged", ctypes.POINTER(ctypes.c_int)), ("phi", ctypes.c_void_p),
                 ("cs", ctypes.c_void_p), ("cl", ctypes.c_void_p), ("cells_per_thread", ctypes.c_int),
-                ("launches", ctypes.c_int64), ("gpu_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64), ("gpu_ms", ctypes.c_double),
+                ("energy", ctypes.POINTER(ctypes.c_double))]
 
 
 class pf_adjoint_desc(ctypes.Structure):
@@ -264,7 +265,7 @@ class Sim:
 def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt=None,
               max_steps=100000, steps_per_launch=500, launches_per_graph=4, check_every=100,
               window=1.0, tol=1e-8, min_travel=0.0, cells_per_thread=0, want_fields=False,
-              stream=None):
+              energy_every=0, stream=None):
     """pf_run_batch: many 1D pulled fronts in one persistent launch per chunk.
 
     pr: shared 1D parameters (workloads.pulled_front_1d style; n, v_pull, dt and
@@ -294,6 +295,7 @@ def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt
     D.max_steps, D.steps_per_launch, D.launches_per_graph = int(max_steps), int(steps_per_launch), int(launches_per_graph)
     D.check_every, D.window, D.tol, D.cells_per_thread = int(check_every), float(window), float(tol), int(cells_per_thread)
     D.min_travel = float(min_travel)
+    D.energy_every = int(energy_every)
     out = dict(k_v=np.zeros(N), dkdt=np.zeros(N), t=np.zeros(N), steps=np.zeros(N, np.int64),
                converged=np.zeros(N, np.int32))
     R = pf_batch_result()
@@ -302,6 +304,9 @@ def run_batch(pr: dict, lengths, v_pull, phi0, cs0, cl0, *, precision="fp32", dt
     R.t = out["t"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     R.steps = out["steps"].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     R.converged = out["converged"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    if energy_every > 0:
+        out["energy"] = np.zeros((N, int(max_steps) // int(energy_every)))
+        R.energy = out["energy"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     if want_fields:
         for k in ("phi", "cs", "cl"):
             out[k] = np.zeros(total, dtype=dtype)

@@ -95,3 +95,24 @@ def test_batch_rejects_invalid():
         pf.run_batch(prs[0], [4], [0.1], phi[:4], cs[:4], cl[:4])
     with pytest.raises(pf.PFError):
         pf.run_batch(prs[0], [64], [-1.0], phi, cs, cl)
+
+
+def test_closed_box_planar_front_with_energy_records():
+    """The 1D planar front (N = 1024, dx = W/4, FP64, no-flux at both ends) as
+    one persistent instance recording F_h after every step: fields and F_h
+    against the oracle, and F_h non-increasing (check (a))."""
+    pr, phi, cs, cl = wl.planar_1d(A=2.0, b=1.0)
+    n, steps = pr["n"][0], 2000
+    res = pf.run_batch(pr, [n], [0.0], phi, cs, cl, precision="fp64", dt=[pr["dt"]], max_steps=steps,
+                       steps_per_launch=500, launches_per_graph=2, check_every=steps, tol=-1.0,
+                       want_fields=True, energy_every=1)
+    st = oracle.State(pr, phi, cs, cl)
+    hist = st.step(steps + 1, energy=True)      # hist[s] = F_h before step s
+    ref = oracle.State(pr, phi, cs, cl)
+    ref.step(steps)
+    for a, b_ in ((res["phi"], ref.phi), (res["cs"], ref.cs), (res["cl"], ref.cl)):
+        assert rel_err(a, b_) <= 1e-11, rel_err(a, b_)
+    E = res["energy"][0]
+    assert np.all(np.isfinite(E))
+    assert np.abs(E - hist[1:steps + 1]).max() <= 1e-12 * np.abs(hist).max()
+    assert np.all(np.diff(E) <= 1e-13 * abs(E[0]))
