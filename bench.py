@@ -65,12 +65,13 @@ SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 # sources the capture ran.  The figure is reported as null as soon as those
 # sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.811776e6 + 231.734272e6) / 256 ** 3,
+    "bytes_per_cell_update": (280.657152e6 + 231.120640e6) / 256 ** 3,
     "captured_grid": 256,
-    "sources": ("pf_step3d.cu", "pf_internal.cuh", "pf_kernels.h"),
-    "sha256": ("33e195e8a4e3313311c95a41d7daee8e0a52812efeee407fa26315e6d8fa3ddc",
+    "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh", "pf_kernels.h"),
+    "sha256": ("b67c57e848978847b670a710cf6d3a1cbe8452cc9b022d4061385d44a448162c",
+               "2135d28c9a255909cf591becabaf9abf4a351101b6479b0b0c3dd55c1ac58e39",
                "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60",
-               "0f6e6d54b674f78de937e97d1348d41647f83bf53000b0ae9aec76ea7aca0a15"),
+               "64188d9010cd0aa9bd6ff6bd07f6a3abcf725fc8eb475da712329986c95aa34f"),
 }
 
 

@@ -19,7 +19,7 @@ struct pf_handle {
     double* dres = nullptr;      // device results (4 doubles)
     double* hres = nullptr;      // pinned host results (4 doubles)
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
-    bool generic3d = false;      // run 3D through the generic kernel (cross-check)
+    bool generic = false;        // run 2D / 3D through the generic kernel (cross-check)
     bool have_front = false;
     double last_xf = 0.0, last_t = 0.0;
     std::string err;
@@ -155,7 +155,7 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     P.shift = params->shift ? 1 : 0;
     h->stream = static_cast<cudaStream_t>(stream);
     if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
-    if (const char* g3 = std::getenv("PF_GENERIC3D")) h->generic3d = std::atoi(g3) != 0;
+    if (const char* g = std::getenv("PF_GENERIC")) h->generic = std::atoi(g) != 0;   // cross-check kernel
 
     const size_t bytes = (size_t)P.cells() * P.elem();
     for (int b = 0; b < 2; ++b) {
@@ -284,7 +284,7 @@ int pf_step(pf_handle* h, int64_t n) {
         a.step = h->step;
         a.shifts = h->shifts;
         a.zchunk = h->zchunk;
-        a.use_generic3d = h->generic3d;
+        a.use_generic = h->generic;
         a.stream = h->stream;
         cudaError_t e = pf::launch_step(a);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");

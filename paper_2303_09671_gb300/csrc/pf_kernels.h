@@ -37,7 +37,7 @@ struct StepLaunch {
     void *phi_out, *c_out, *d_out, *clo_out;
     int64_t step, shifts;   // clock of the input state
     int zchunk;             // planes per CTA along z (3D); <= 0: automatic
-    bool use_generic3d;     // 3D: the generic (1D/2D/3D) kernel instead of the 3D one
+    bool use_generic;       // 2D / 3D: the generic (1D/2D/3D) kernel instead of the paired one
     cudaStream_t stream;
 };
 

@@ -56,6 +56,8 @@ struct Tile {
 // at the face phi.
 template <typename T>
 cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K);
+template <typename T>
+cudaError_t launch_step2d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& K);
 
 template <typename T, int DIM>
 __device__ __forceinline__ void face_flux(const Consts<T>& C, int axis,
@@ -517,8 +519,8 @@ static cudaError_t launch_T(const StepLaunch& a) {
     const Consts<T> C = make_consts<T>(P);
     const Clock<T> K = make_clock<T>(P, a.step, a.shifts);
     if (P.dim == 1) return launch_tile<T, 1, 128, 1>(a, C, K);
-    if (P.dim == 2) return launch_tile<T, 2, 32, 8>(a, C, K);
-    if (a.use_generic3d) return launch_tile<T, 3, 32, 8>(a, C, K);
+    if (P.dim == 2) return a.use_generic ? launch_tile<T, 2, 32, 8>(a, C, K) : launch_step2d<T>(a, C, K);
+    if (a.use_generic) return launch_tile<T, 3, 32, 8>(a, C, K);
     return launch_step3d<T>(a, C, K);
 }
 

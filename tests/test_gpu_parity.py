@@ -104,6 +104,22 @@ def test_fp64_2d_random(bc, lap, A, nsteps):
     assert_fields(st, g, TOL64, pr)
 
 
+@pytest.mark.parametrize("bc_lo,bc_hi,lap", [
+    (("periodic", "noflux"), ("periodic", "dirichlet"), 9),
+    (("periodic", "noflux"), ("periodic", "noflux"), 5),
+])
+def test_fp64_2d_wide_ragged_front_along_y(bc_lo, bc_hi, lap):
+    """163 x 51 with the front running along x (solid at low y): six x tiles and
+    four y tiles of the paired kernel, both ragged, an odd row count (the last
+    pair has one live lane), periodic x ends and a Dirichlet or no-flux top."""
+    pr, *_ = wl.random_state(2, (163, 51), dx=0.5, A=1.2, b=0.3, a=-0.3, seed=12,
+                             bc_lo=bc_lo, bc_hi=bc_hi, lap=lap)
+    _, phi, cs, cl = wl.random_state(2, (51, 163), dx=0.5, A=1.2, b=0.3, a=-0.3, seed=12, lap=lap)
+    phi, cs, cl = (np.ascontiguousarray(a.T) for a in (phi, cs, cl))
+    st, g, _ = run_pair(pr, phi, cs, cl, 40)
+    assert_fields(st, g, TOL64, pr)
+
+
 def test_fp64_2d_dirichlet_and_temperature():
     pr, phi, cs, cl = wl.random_state(2, (45, 19), dx=0.5, A=1.5, b=0.3, seed=6,
                                       bc_lo=("noflux", "periodic"), bc_hi=("dirichlet", "periodic"),
