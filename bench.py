@@ -61,17 +61,16 @@ BYTES_PER_CELL_UPDATE = 24          # FP32 read + write of phi, c_s, c_l (algori
 SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step3d_kernel
-# launch from an ncu capture, per cell-update, and the SHA-256 of the kernel
-# sources the capture ran.  The figure is reported as null as soon as those
-# sources differ from the ones captured.
+# launch from an ncu capture, per cell-update, and the SHA-256 of the sources
+# of the kernel's device code the capture ran.  The figure is reported as null
+# as soon as those sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
     "bytes_per_cell_update": (280.657152e6 + 231.120640e6) / 256 ** 3,
     "captured_grid": 256,
-    "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh", "pf_kernels.h"),
+    "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh"),
     "sha256": ("b67c57e848978847b670a710cf6d3a1cbe8452cc9b022d4061385d44a448162c",
                "2135d28c9a255909cf591becabaf9abf4a351101b6479b0b0c3dd55c1ac58e39",
-               "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60",
-               "64188d9010cd0aa9bd6ff6bd07f6a3abcf725fc8eb475da712329986c95aa34f"),
+               "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60"),
 }
 
 

@@ -12,7 +12,8 @@
 struct pf_handle {
     pf::HostProblem P;
     cudaStream_t stream = nullptr;
-    pf::Fields buf[2] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    pf::Fields buf[2] = {{nullptr, nullptr, nullptr, nullptr, nullptr},
+                         {nullptr, nullptr, nullptr, nullptr, nullptr}};
     int cur = 0;
     int64_t step = 0, shifts = 0;
     double* scratch = nullptr;   // diagnostics partials
@@ -159,8 +160,9 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
 
     const size_t bytes = (size_t)P.cells() * P.elem();
     for (int b = 0; b < 2; ++b) {
-        void** slots[4] = {&h->buf[b].phi, &h->buf[b].c, &h->buf[b].d, &h->buf[b].clo};
-        const int nf = (P.precision == PF_FP32) ? 4 : 3;   // FP32 keeps the low word of c
+        void** slots[5] = {&h->buf[b].phi, &h->buf[b].c, &h->buf[b].d, &h->buf[b].clo, &h->buf[b].plo};
+        // FP32 keeps the low word of c, and in 1D also that of phi
+        const int nf = (P.precision == PF_FP32) ? (P.dim == 1 ? 5 : 4) : 3;
         for (int f = 0; f < nf; ++f) {
             cudaError_t e = cudaMalloc(slots[f], bytes);
             if (e != cudaSuccess) {
@@ -188,7 +190,7 @@ void pf_destroy(pf_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     for (int b = 0; b < 2; ++b) {
-        void* slots[4] = {h->buf[b].phi, h->buf[b].c, h->buf[b].d, h->buf[b].clo};
+        void* slots[5] = {h->buf[b].phi, h->buf[b].c, h->buf[b].d, h->buf[b].clo, h->buf[b].plo};
         for (void* p : slots)
             if (p) cudaFree(p);
     }
@@ -279,8 +281,8 @@ int pf_step(pf_handle* h, int64_t n) {
         const pf::Fields& out = h->buf[h->cur ^ 1];
         pf::StepLaunch a;
         a.prob = &P;
-        a.phi_in = in.phi; a.c_in = in.c; a.d_in = in.d; a.clo_in = in.clo;
-        a.phi_out = out.phi; a.c_out = out.c; a.d_out = out.d; a.clo_out = out.clo;
+        a.phi_in = in.phi; a.c_in = in.c; a.d_in = in.d; a.clo_in = in.clo; a.plo_in = in.plo;
+        a.phi_out = out.phi; a.c_out = out.c; a.d_out = out.d; a.clo_out = out.clo; a.plo_out = out.plo;
         a.step = h->step;
         a.shifts = h->shifts;
         a.zchunk = h->zchunk;

@@ -183,18 +183,20 @@ __device__ __forceinline__ void put_c(T* c, T* clo, long long i, double v) {
 }
 
 template <typename T>
-__global__ void shift_kernel(StateView<T> in, T* po, T* co, T* dout, T* clo_out, int n,
-                             double fphi, double fc, double fd) {
+__global__ void shift_kernel(StateView<T> in, const T* plo_in, T* po, T* co, T* dout, T* clo_out,
+                             T* plo_out, int n, double fphi, double fc, double fd) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (i < n - 1) {
             po[i] = in.phi[i + 1];
             co[i] = in.c[i + 1];
             dout[i] = in.d[i + 1];
             if (clo_out) clo_out[i] = in.clo[i + 1];
+            if (plo_out) plo_out[i] = plo_in[i + 1];
         } else {
             po[i] = (T)fphi;
             dout[i] = (T)fd;
             put_c(co, clo_out, i, fc);
+            if (plo_out) plo_out[i] = (T)(fphi - (double)(T)fphi);
         }
     }
 }
@@ -228,7 +230,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __global__ void __launch_bounds__(DIAG_THREADS)
 to_state_f32_kernel(const float* __restrict__ phi, const float* __restrict__ cs,
                     const float* __restrict__ cl, long long n, DiagConsts C, float* __restrict__ po,
-                    float* __restrict__ co, float* __restrict__ dout, float* __restrict__ clo) {
+                    float* __restrict__ co, float* __restrict__ dout, float* __restrict__ clo,
+                    float* __restrict__ plo) {
     const float a = (float)C.a;
     const bool cubic = C.interp == 1;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -246,6 +249,7 @@ to_state_f32_kernel(const float* __restrict__ phi, const float* __restrict__ cs,
         const float lo = e + small;
         const float c = hi + lo;
         po[i] = f;
+        if (plo) plo[i] = 0.0f;
         co[i] = c;
         clo[i] = lo - (c - hi);
         dout[i] = dh;
@@ -367,11 +371,13 @@ cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& o
     const double p = p_host(P, P.dir_phi);
     const double fc = p * P.dir_cs + (1.0 - p) * P.dir_cl, fd = P.dir_cs - P.dir_cl;
     if (P.precision == 1)
-        shift_kernel<double><<<blocks, 256, 0, s>>>(view<double>(in), (double*)out.phi, (double*)out.c,
-                                                    (double*)out.d, nullptr, n, P.dir_phi, fc, fd);
+        shift_kernel<double><<<blocks, 256, 0, s>>>(view<double>(in), nullptr, (double*)out.phi,
+                                                    (double*)out.c, (double*)out.d, nullptr, nullptr, n,
+                                                    P.dir_phi, fc, fd);
     else
-        shift_kernel<float><<<blocks, 256, 0, s>>>(view<float>(in), (float*)out.phi, (float*)out.c,
-                                                   (float*)out.d, (float*)out.clo, n, P.dir_phi, fc, fd);
+        shift_kernel<float><<<blocks, 256, 0, s>>>(view<float>(in), (const float*)in.plo, (float*)out.phi,
+                                                   (float*)out.c, (float*)out.d, (float*)out.clo,
+                                                   (float*)out.plo, n, P.dir_phi, fc, fd);
     return cudaGetLastError();
 }
 
@@ -386,7 +392,7 @@ cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* c
     else
         to_state_f32_kernel<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
             (const float*)phi, (const float*)cs, (const float*)cl, n, C, (float*)out.phi,
-            (float*)out.c, (float*)out.d, (float*)out.clo);
+            (float*)out.c, (float*)out.d, (float*)out.clo, (float*)out.plo);
     return cudaGetLastError();
 }
 

@@ -26,15 +26,18 @@ struct HostProblem {
 };
 
 // Device state: phi, c = p c_s + (1-p) c_l, d = c_s - c_l and, in FP32, the
-// low word c_lo of c (NULL in FP64).
+// low word c_lo of c (NULL in FP64).  A 1D FP32 state also keeps the low word
+// phi_lo of phi (NULL otherwise): there the rounding of phi to FP32 after
+// every step, accumulated over the slow motion of a planar front, is the
+// largest FP32 error.
 struct Fields {
-    void *phi, *c, *d, *clo;
+    void *phi, *c, *d, *clo, *plo;
 };
 
 struct StepLaunch {
     const HostProblem* prob;
-    const void *phi_in, *c_in, *d_in, *clo_in;
-    void *phi_out, *c_out, *d_out, *clo_out;
+    const void *phi_in, *c_in, *d_in, *clo_in, *plo_in;
+    void *phi_out, *c_out, *d_out, *clo_out, *plo_out;
     int64_t step, shifts;   // clock of the input state
     int zchunk;             // planes per CTA along z (3D); <= 0: automatic
     bool use_generic;       // 2D / 3D: the generic (1D/2D/3D) kernel instead of the paired one

@@ -105,9 +105,9 @@ __device__ __forceinline__ void face_flux(const Consts<T>& C, int axis,
 template <typename T, int DIM, int TX, int TY>
 __global__ void __launch_bounds__(TX *(DIM >= 2 ? TY : 1))
 step_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in,
-            const T* __restrict__ d_in, const T* __restrict__ clo_in,
+            const T* __restrict__ d_in, const T* __restrict__ clo_in, const T* __restrict__ plo_in,
             T* __restrict__ phi_out, T* __restrict__ c_out, T* __restrict__ d_out,
-            T* __restrict__ clo_out, Consts<T> C, Clock<T> K, int zchunk) {
+            T* __restrict__ clo_out, T* __restrict__ plo_out, Consts<T> C, Clock<T> K, int zchunk) {
     using L = Tile<T, DIM, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -369,7 +369,18 @@ step_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in,
         const long long gi = (long long)z * sz + (long long)gy * sy + gx;
         const T f = RAW(0, s0, h);
         const T dcv = C.dt * dc * C.inv_dx;
-        phi_out[gi] = f + C.dt * PD(g0, r);
+        if (plo_in != nullptr) {
+            // phi = hi + lo, the increment added by TwoSum as for c below
+            const T dp = C.dt * PD(g0, r);
+            const T s = f + dp;
+            const T bv = s - f;
+            const T lo = plo_in[gi] + ((f - (s - bv)) + (dp - bv));
+            const T hi = s + lo;
+            phi_out[gi] = hi;
+            plo_out[gi] = lo - (hi - s);
+        } else {
+            phi_out[gi] = f + C.dt * PD(g0, r);
+        }
         d_out[gi] = d_in[gi] + C.dt * dd * C.inv_dx;
         const T c = c_in[gi];
         if (clo_in != nullptr) {
@@ -471,9 +482,9 @@ static cudaError_t launch_tile(const StepLaunch& a, const Consts<T>& C, const Cl
     }
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in),
-        static_cast<const T*>(a.d_in), static_cast<const T*>(a.clo_in),
+        static_cast<const T*>(a.d_in), static_cast<const T*>(a.clo_in), static_cast<const T*>(a.plo_in),
         static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out), static_cast<T*>(a.d_out),
-        static_cast<T*>(a.clo_out), C, K, zchunk);
+        static_cast<T*>(a.clo_out), static_cast<T*>(a.plo_out), C, K, zchunk);
     return cudaGetLastError();
 }
 

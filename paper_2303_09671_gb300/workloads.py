@@ -143,6 +143,35 @@ def perturbed_front_2d(nx=1024, ny=1024, dx=0.5, k_e=0.15, u=0.3, D_s=1e-3, fron
     return pr, phi, cs, cl
 
 
+def perturbed_front_3d(nx=64, ny=48, nz=40, dx=0.5, k_e=0.15, u=0.3, D_s=1e-3, front=20, modes=6,
+                       amp_cells=2.0, seed=21, **kw):
+    """3D planar front with a seeded perturbation: the 2D recipe above extruded
+    to a second transverse axis.  Growth along x (no-flux); y and z periodic;
+    x_f(y, z) = front + sum_m a_m cos(2 pi (k_m y / ny + l_m z / nz) + psi_m)
+    cells with integer (k_m, l_m), wavelengths of at least 16 cells, scaled so
+    that max |x_f - front| = amp_cells."""
+    rng = np.random.default_rng(seed)
+    theta = theta_from_undercooling(k_e, u)
+    kw.setdefault("bc_lo", ("noflux", "periodic", "periodic"))
+    kw.setdefault("bc_hi", ("noflux", "periodic", "periodic"))
+    pr = scaled_params(3, (nx, ny, nz), dx, k_e, theta, D_s, **kw)
+    ky = rng.integers(0, max(1, ny // 16) + 1, size=modes)
+    kz = rng.integers(0, max(1, nz // 16) + 1, size=modes)
+    kz[(ky == 0) & (kz == 0)] = 1
+    am = rng.uniform(0.5, 1.0, size=modes)
+    ps = rng.uniform(0, 2 * math.pi, size=modes)
+    yy, zz = np.meshgrid(np.arange(ny), np.arange(nz), indexing="xy")      # shape (nz, ny)
+    pert = sum(a * np.cos(2 * math.pi * (k * yy / ny + l * zz / nz) + q)
+               for a, k, l, q in zip(am, ky, kz, ps))
+    pert *= amp_cells / np.abs(pert).max()
+    xf = (front + pert) * dx                                               # per (z, y)
+    x = cell_centres(nx, dx)
+    phi = tanh_profile(x[None, None, :], xf[:, :, None])                   # shape (nz, ny, nx)
+    cs = np.full(phi.shape, k_e * pr["c_inf"])
+    cl = np.full(phi.shape, pr["c_inf"])
+    return pr, phi, cs, cl
+
+
 def sphere_seed_3d(n=256, dx=0.5, k_e=0.1, u=0.5, D_s=1e-4, radius_cells=20.0, modes=8,
                    noise_cells=1.0, seed=3, **kw):
     """3D spherical solid seed with seeded surface noise at the box centre.
