@@ -65,7 +65,8 @@ template <typename V>
 struct PairConsts {
     V one, two, half, sixteenth, sixteenth_neg, third, sixth, four, six;
     V h2, h3, h4, h5, dh1, dh2, dh3, dh4, a_int;
-    V Ms_c, Ms_0, Ml_c, Ml_0, b, A, one_m_A, half_one_m_A, one_m_ke, log_ke;
+    V Ms_c, Ms_0, Ml_c, Ml_0, b, A, one_m_A, one_m_ke, log_ke;
+    V Ms_c_half, Ml_c_half, quarter_one_m_A;   // for face sums in place of face means
     V sigma, H, dx2, inv_Mphi, K_anti, delta2_dx2, delta2_4dx2, dt_dx2;
 };
 
@@ -90,17 +91,21 @@ __device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// p(phi) of Eq. interpolation2 and its derivative, two lanes
-template <typename V>
+// p(phi) of Eq. interpolation2 and its derivative, two lanes.  AI = false: the
+// shape parameter a is 0 and p = h (the term a (phi - 1/2) phi^2 (1-phi)^2 is
+// skipped, which leaves the result bit for bit the same)
+template <bool AI = true, typename V>
 __device__ __forceinline__ V vp_of(const PairConsts<V>& K, V f) {
-    const V g = vmul(f, vsub(K.one, f));
     const V h = vmul(vmul(f, f), vfma(f, vfma(f, vfma(f, K.h5, K.h4), K.h3), K.h2));
+    if constexpr (!AI) return h;
+    const V g = vmul(f, vsub(K.one, f));
     return vfma(vmul(K.a_int, vsub(f, K.half)), vmul(g, g), h);
 }
-template <typename V>
+template <bool AI = true, typename V>
 __device__ __forceinline__ V vdp_of(const PairConsts<V>& K, V f) {
-    const V g = vmul(f, vsub(K.one, f));
     const V dh = vmul(f, vfma(f, vfma(f, vfma(f, K.dh4, K.dh3), K.dh2), K.dh1));
+    if constexpr (!AI) return dh;
+    const V g = vmul(f, vsub(K.one, f));
     // d/dphi [g^2 (phi - 1/2)] = g^2 + 2 g (1 - 2 phi)(phi - 1/2) = g^2 - 4 g (phi - 1/2)^2
     const V s = vsub(f, K.half);
     const V w = vmul(g, vsub(g, vmul(K.four, vmul(s, s))));
@@ -108,7 +113,10 @@ __device__ __forceinline__ V vdp_of(const PairConsts<V>& K, V f) {
 }
 
 // Fluxes through a face (dx times F_c, F_d of the model) from the face state:
-// f, c_s, c_l = face means; pds = sum of the two cells' dx^2 phidot; n = the
+// f = face mean of phi; cs2, cl2 = the sums (twice the face means) of c_s and
+// c_l, taken by constants halved on the host (M_s = M_s_c c_s + M_s_0 becomes
+// (M_s_c / 2) cs2 + M_s_0; exact, since halving is); pds = sum of the two
+// cells' dx^2 phidot; n = the
 // normal differences R - L of {phi, Y, mu_s, mu_l}; t1, t2 = the transverse
 // sums of four centred differences (4 dx times the face's transverse
 // gradient).  With T_i = M_i [n_i (|t|^2/16 + delta^2 dx^2) - n_phi (t.t_i)/16]
@@ -117,13 +125,13 @@ __device__ __forceinline__ V vdp_of(const PairConsts<V>& K, V f) {
 //   F_d = r [T_s - T_l + at],  at = (1-A) d phidot dx^2 n_phi,
 //   r = 1/(n_phi^2 + |t|^2/16 + delta^2 dx^2)
 // T2 = false: a face of a 2D grid, with one transverse direction (t2 unused)
-template <typename V, bool T2 = true>
-__device__ __forceinline__ void face_flux(const PairConsts<V>& K, V f, V cs, V cl, V pds, const V n[4],
+template <typename V, bool T2 = true, bool AI = true>
+__device__ __forceinline__ void face_flux(const PairConsts<V>& K, V f, V cs2, V cl2, V pds, const V n[4],
                                           const V t1[4], const V t2[4], V& Fc, V& Fd) {
-    const V d = vsub(cs, cl);
-    const V p = vp_of(K, f);
+    const V d2 = vsub(cs2, cl2);   // twice the face d
+    const V p = vp_of<AI>(K, f);
     const V omp = vsub(K.one, p);
-    const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
+    const V Ms = vfma(K.Ms_c_half, cs2, K.Ms_0), Ml = vfma(K.Ml_c_half, cl2, K.Ml_0);
     const V bMl = vmul(K.b, Ml);
     const V iMbar = vrcp(vfma(bMl, p, vmul(Ms, omp)));
     const V tt = T2 ? vfma(t1[0], t1[0], vmul(t2[0], t2[0])) : vmul(t1[0], t1[0]);
@@ -136,7 +144,7 @@ __device__ __forceinline__ void face_flux(const PairConsts<V>& K, V f, V cs, V c
     const V tl = T2 ? vfma(t1[0], t1[3], vmul(t2[0], t2[3])) : vmul(t1[0], t1[3]);
     const V Ts = vmul(Ms, vfma(m, ts, vmul(n[2], gt2d)));
     const V Tl = vmul(Ml, vfma(m, tl, vmul(n[3], gt2d)));
-    const V at = vmul(vmul(K.half_one_m_A, pds), vmul(d, n[0]));
+    const V at = vmul(vmul(K.quarter_one_m_A, pds), vmul(d2, n[0]));
     const V pomp = vmul(p, omp);
     const V q = vmul(vmul(Ms, Ml), vmul(vfma(K.b, p, omp), iMbar));
     const V afn = vmul(vsub(Ms, bMl), vmul(pomp, iMbar));
@@ -182,7 +190,8 @@ inline PairConsts<typename Lanes<T>::V> make_pair_consts(const HostProblem& P, c
     K.dh1 = S(C.dh1); K.dh2 = S(C.dh2); K.dh3 = S(C.dh3); K.dh4 = S(C.dh4);
     K.a_int = S(P.a);
     K.Ms_c = S(C.Ms_c); K.Ms_0 = S(C.Ms_0); K.Ml_c = S(C.Ml_c); K.Ml_0 = S(C.Ml_0);
-    K.b = S(P.b); K.A = S(P.A); K.one_m_A = S(1.0 - P.A); K.half_one_m_A = S(0.5 * (1.0 - P.A));
+    K.b = S(P.b); K.A = S(P.A); K.one_m_A = S(1.0 - P.A);
+    K.Ms_c_half = S(0.5 * C.Ms_c); K.Ml_c_half = S(0.5 * C.Ml_c); K.quarter_one_m_A = S(0.25 * (1.0 - P.A));
     K.one_m_ke = S(1.0 - P.k_e); K.log_ke = S(std::log(P.k_e));
     const double dx2 = P.dx * P.dx;
     K.sigma = S(P.sigma); K.H = S(P.H); K.dx2 = S(dx2); K.inv_Mphi = S(1.0 / P.M_phi);

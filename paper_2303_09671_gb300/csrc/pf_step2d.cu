@@ -48,7 +48,7 @@ struct PTile2 {
     static constexpr size_t BYTES = OFF_FY + sizeof(V) * (TYP + 1) * TX;
 };
 
-template <typename T, int TX, int TY, bool L9>
+template <typename T, int TX, int TY, bool L9, bool AI>
 __global__ void __launch_bounds__(TX * (TY / 2), sizeof(T) == 4 ? 2 : 1)
 step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
               const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
@@ -114,7 +114,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             }
         }
         const V f = vpair(f2[0], f2[1]), c = vpair(c2[0], c2[1]), d = vpair(d2[0], d2[1]);
-        const V p = vp_of(K, f);
+        const V p = vp_of<AI>(K, f);
         const V cs = vfma(vsub(K.one, p), d, c);
         const V cl = vsub(c, vmul(p, d));
         const V mus = vsub(vlog(cs), K.log_ke);
@@ -157,7 +157,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V sx = vsub(bxp.a, bxm.a), sy = vpair(bc.a.y - bS.a.y, bN.a.x - bc.a.x);
         const V lx = vsub(bxp.b, bxm.b), ly = vpair(bc.b.y - bS.b.y, bN.b.x - bc.b.x);
         const V cs = cc.a, cl = cc.b, mus = bc.a, mul = bc.b;
-        const V p = vp_of(K, f), dp = vdp_of(K, f);
+        const V p = vp_of<AI>(K, f), dp = vdp_of<AI>(K, f);
         const V omp = vsub(K.one, p);
         const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
         const V bMl = vmul(K.b, Ml);
@@ -209,7 +209,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 #pragma unroll
         for (int k = 0; k < 4; ++k) t1[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
         const Q cL = sC[hL], cR = sC[hR];
-        face_flux<V, false>(K, vmul(K.half, SP[0]), vmul(K.half, vadd(cL.a, cR.a)), vmul(K.half, vadd(cL.b, cR.b)),
+        face_flux<V, false, AI>(K, vmul(K.half, SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
                             vadd(sD[rL], sD[rL + 1]), n, t1, t1, Fc, Fd);
     };
     // y faces above the two rows of the pair at hL: lanes (y+1/2, y+3/2)
@@ -231,9 +231,9 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const Q cP_ = sC[hL], cN_ = sC[hN];
         const V dP = sD[rL], dN = sD[rL + RX];
         const V f = vmul(K.half, vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
-        const V cs = vmul(K.half, vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x));
-        const V cl = vmul(K.half, vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x));
-        face_flux<V, false>(K, f, cs, cl, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t1, Fc, Fd);
+        const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
+        const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
+        face_flux<V, false, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t1, Fc, Fd);
     };
     const bool nf_x = own_x == nx - 1 && G.bc_hi[0] == BC_NOFLUX;
     const bool nf_ylo = own_y == ny - 1 && G.bc_hi[1] == BC_NOFLUX;
@@ -302,8 +302,10 @@ template <typename T>
 cudaError_t launch_step2d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& Kc) {
     constexpr int TX = 32, TY = 16;
     using L = PTile2<T, TX, TY>;
-    auto k9 = step2d_kernel<T, TX, TY, true>;
-    auto k5 = step2d_kernel<T, TX, TY, false>;
+    // 9- or 5-point Laplacian x shape parameter a != 0 or a = 0
+    decltype(&step2d_kernel<T, TX, TY, true, true>) kerns[2][2] = {
+        {step2d_kernel<T, TX, TY, false, false>, step2d_kernel<T, TX, TY, false, true>},
+        {step2d_kernel<T, TX, TY, true, false>, step2d_kernel<T, TX, TY, true, true>}};
     static DeviceSetup setup;
     {
         int dev = 0;
@@ -312,8 +314,9 @@ cudaError_t launch_step2d(const StepLaunch& a, const Consts<T>& C, const Clock<T
         if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
         std::lock_guard<std::mutex> lock(setup.mu);
         if (!setup.done[dev]) {
-            e = cudaFuncSetAttribute(k9, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+                e = cudaFuncSetAttribute(kerns[i / 2][i % 2], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::BYTES);
             if (e != cudaSuccess) return e;
             setup.done[dev] = true;
         }
@@ -323,7 +326,7 @@ cudaError_t launch_step2d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     const GridConsts<T> G = make_grid_consts<T>(P, Kc);
     const dim3 block(L::NT);
     const dim3 grid((C.n[0] + TX - 1) / TX, (C.n[1] + TY - 1) / TY, 1);
-    auto kern = (C.lap == 9) ? k9 : k5;
+    auto kern = kerns[C.lap == 9 ? 1 : 0][P.a != 0.0 ? 1 : 0];
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),

@@ -70,7 +70,7 @@ struct PTile {
 
 __device__ __forceinline__ int slot3(int z) { return ((z % 3) + 3) % 3; }
 
-template <typename T, int TX, int TY, bool L19>
+template <typename T, int TX, int TY, bool L19, bool AI>
 __global__ void __launch_bounds__(TX * (TY / 2), (sizeof(T) == 4 ? 2 : 1))
 step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
               const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
@@ -207,7 +207,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             if ((j + 1) * NT > NH && hl >= NH) break;
             const V f = R[hl], c = R[NHP + hl], d = R[2 * NHP + hl];
             const int h = hring[j];
-            const V p = vp_of(K, f);
+            const V p = vp_of<AI>(K, f);
             const V cs = vfma(vsub(K.one, p), d, c);
             const V cl = vsub(c, vmul(p, d));
             const V mus = vsub(vlog(cs), K.log_ke);
@@ -259,7 +259,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V sx = vsub(bxp.a, bxm.a), sy = vpair(bc.a.y - bS.a.y, bN.a.x - bc.a.x), sz_ = vsub(bzp.a, bzm.a);
             const V lx = vsub(bxp.b, bxm.b), ly = vpair(bc.b.y - bS.b.y, bN.b.x - bc.b.x), lz = vsub(bzp.b, bzm.b);
             const V cs = cc.a, cl = cc.b, mus = bc.a, mul = bc.b;
-            const V p = vp_of(K, f), dp = vdp_of(K, f);
+            const V p = vp_of<AI>(K, f), dp = vdp_of<AI>(K, f);
             const V omp = vsub(K.one, p);
             const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
             const V bMl = vmul(K.b, Ml);
@@ -324,7 +324,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         t2[2] = vsub(vadd(bPL.a, bPR.a), vadd(bML.a, bMR.a));
         t2[3] = vsub(vadd(bPL.b, bPR.b), vadd(bML.b, bMR.b));
         const Q cL = C0[hL], cR = C0[hR];
-        face_flux(K, vmul(K.half, SP[0]), vmul(K.half, vadd(cL.a, cR.a)), vmul(K.half, vadd(cL.b, cR.b)),
+        face_flux<V, true, AI>(K, vmul(K.half, SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
                   vadd(D0[rL], D0[rL + 1]), n, t1, t2, Fc, Fd);
     };
     // y faces above the two rows of the pair at hL: lanes (y+1/2, y+3/2)
@@ -360,9 +360,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const Q cP_ = C0[hL], cN_ = C0[hN];
         const V dP = D0[rL], dN = D0[rL + RX];
         const V f = vmul(K.half, vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
-        const V cs = vmul(K.half, vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x));
-        const V cl = vmul(K.half, vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x));
-        face_flux(K, f, cs, cl, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
+        const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
+        const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
+        face_flux<V, true, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
     };
     // z face between planes z and z+1 of the pair at h (ring index r)
     auto zface = [&](int z, int h, int r, V& Fc, V& Fd) {
@@ -395,7 +395,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             for (int k = 0; k < 4; ++k) t2[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
         }
         const Q c0 = C0[h], c1 = C1[h];
-        face_flux(K, vmul(K.half, vadd(a0.a, a1.a)), vmul(K.half, vadd(c0.a, c1.a)), vmul(K.half, vadd(c0.b, c1.b)),
+        face_flux<V, true, AI>(K, vmul(K.half, vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
                   vadd(D0[r], D1[r]), n, t1, t2, Fc, Fd);
     };
     auto z_noflux = [&](int z) {
@@ -539,8 +539,10 @@ template <typename T>
 cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& Kc) {
     constexpr int TX = 32, TY = 16;
     using L = PTile<T, TX, TY>;
-    auto k19 = step3d_kernel<T, TX, TY, true>;
-    auto k7 = step3d_kernel<T, TX, TY, false>;
+    // 19- or 7-point Laplacian x shape parameter a != 0 or a = 0
+    decltype(&step3d_kernel<T, TX, TY, true, true>) kerns[2][2] = {
+        {step3d_kernel<T, TX, TY, false, false>, step3d_kernel<T, TX, TY, false, true>},
+        {step3d_kernel<T, TX, TY, true, false>, step3d_kernel<T, TX, TY, true, true>}};
     static DeviceSetup setup;
     int dev = 0, per_sm = 1, sms = 1;
     {
@@ -549,12 +551,13 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
         if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
         std::lock_guard<std::mutex> lock(setup.mu);
         if (!setup.done[dev]) {
-            e = cudaFuncSetAttribute(k19, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+                e = cudaFuncSetAttribute(kerns[i / 2][i % 2], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::BYTES);
             if (e != cudaSuccess) return e;
             int s = 1, p = 1;
             cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k19, L::NT, L::BYTES);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kerns[1][1], L::NT, L::BYTES);
             setup.sms[dev] = s;
             setup.per_sm[dev] = p < 1 ? 1 : p;
             setup.done[dev] = true;
@@ -570,7 +573,7 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     int zchunk = a.zchunk;
     if (zchunk <= 0) zchunk = choose_zchunk((long long)grid.x * grid.y, C.n[2], (long long)per_sm * sms);
     grid.z = (C.n[2] + zchunk - 1) / zchunk;
-    auto kern = (C.lap == 19) ? k19 : k7;
+    auto kern = kerns[C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
