@@ -49,7 +49,7 @@ struct PTile2 {
 };
 
 template <typename T, int TX, int TY, bool L9, bool AI>
-__global__ void __launch_bounds__(TX * (TY / 2), sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TX * (TY / 2), sizeof(T) == 4 ? 3 : 1)
 step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
               const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
               T* __restrict__ d_out, T* __restrict__ clo_out, const PairConsts<typename Lanes<T>::V> K,
