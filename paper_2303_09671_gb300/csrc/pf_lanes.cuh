@@ -38,9 +38,22 @@ __device__ __forceinline__ float2 vsub(float2 a, float2 b) {
     memcpy(&r, &rr, 8);
     return r;
 }
-__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
-// the hardware-approximated logarithm (a few ulp; the FP64 path is exact)
-__device__ __forceinline__ float2 vlog(float2 a) { return make_float2(__logf(a.x), __logf(a.y)); }
+// FP32 reciprocal and natural logarithm from the PTX approximate instructions
+// (rcp.approx, lg2.approx; flush-to-zero, as every operand here is a normal
+// number of moderate size): 1/x to ~1 ulp, ln x = ln 2 log2 x to ~2^-22
+// relative.  The FP64 path below is exact IEEE.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ln_fast(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * 0.693147180559945309f;
+}
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(rcp_fast(a.x), rcp_fast(a.y)); }
+__device__ __forceinline__ float2 vlog(float2 a) { return make_float2(ln_fast(a.x), ln_fast(a.y)); }
 __device__ __forceinline__ float2 vpair(float a, float b) { return make_float2(a, b); }
 
 __device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
