@@ -65,11 +65,11 @@ SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 # of the kernel's device code the capture ran.  The figure is reported as null
 # as soon as those sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.657152e6 + 231.120640e6) / 256 ** 3,
+    "bytes_per_cell_update": (281.502464e6 + 229.926656e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh"),
-    "sha256": ("b67c57e848978847b670a710cf6d3a1cbe8452cc9b022d4061385d44a448162c",
-               "2135d28c9a255909cf591becabaf9abf4a351101b6479b0b0c3dd55c1ac58e39",
+    "sha256": ("c3145a22632a1ecde92e83b1096b3c34c750053b766cef5e55e8544b9016d66c",
+               "ca8a8936b55cf3a8d7bbbc6ef71bd5cec65b4f4c0f6931f1105397cc5e2714b8",
                "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60"),
 }
 

@@ -115,7 +115,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         }
         const V f = vpair(f2[0], f2[1]), c = vpair(c2[0], c2[1]), d = vpair(d2[0], d2[1]);
         const V p = vp_of<AI>(K, f);
-        const V cs = vfma(vsub(K.one, p), d, c);
+        const V cs = vfma(vsub(vlit<V>(1.0), p), d, c);
         const V cl = vsub(c, vmul(p, d));
         const V mus = vsub(vlog(cs), K.log_ke);
         const V mul = vlog(cl);
@@ -146,9 +146,9 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V XS = vadd(sP[hS - 1], sP[hS + 1]), XN = vadd(sP[hN - 1], sP[hN + 1]);
             const V corners = vpair(XS.y + XP.y, XP.x + XN.x);
             // [4 faces + corners - 20 centre] / 6
-            lap = vmul(K.sixth, vfma(K.four, vsub(faces, vfma(K.four, f, f)), corners));
+            lap = vmul(vlit<V>((1.0 / 6)), vfma(vlit<V>(4.0), vsub(faces, vfma(vlit<V>(4.0), f, f)), corners));
         } else {
-            lap = vsub(faces, vmul(K.four, f));
+            lap = vsub(faces, vmul(vlit<V>(4.0), f));
         }
         const Q cc = sC[h], bc = sB[h];
         const Q bxm = sB[h - 1], bxp = sB[h + 1], bS = sB[hS], bN = sB[hN];
@@ -158,7 +158,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V lx = vsub(bxp.b, bxm.b), ly = vpair(bc.b.y - bS.b.y, bN.b.x - bc.b.x);
         const V cs = cc.a, cl = cc.b, mus = bc.a, mul = bc.b;
         const V p = vp_of<AI>(K, f), dp = vdp_of<AI>(K, f);
-        const V omp = vsub(K.one, p);
+        const V omp = vsub(vlit<V>(1.0), p);
         const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
         const V bMl = vmul(K.b, Ml);
         const V Msq = vmul(Ms, omp);
@@ -174,11 +174,11 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V theta = vpair(th_s, th_s);
         const V dmu = vsub(mus, mul);
         // D = [M_s (1-p)(1 - A(1-p)) + A b M_l p^2] / Mbar
-        const V Dd = vmul(vfma(Msq, vsub(K.one, vmul(K.A, omp)), vmul(vmul(K.A, bMl), vmul(p, p))), iMbar);
+        const V Dd = vmul(vfma(Msq, vsub(vlit<V>(1.0), vmul(K.A, omp)), vmul(vmul(K.A, bMl), vmul(p, p))), iMbar);
         // DeltaG = c_s (mu_s - mu_l) - d - (1-k_e) theta - D d (mu_s - mu_l)
         const V dG = vsub(vsub(vmul(cs, dmu), d), vfma(K.one_m_ke, theta, vmul(vmul(Dd, d), dmu)));
-        const V g = vmul(f, vsub(K.one, f));
-        const V dfdw = vmul(g, vsub(K.two, vmul(K.four, f)));
+        const V g = vmul(f, vsub(vlit<V>(1.0), f));
+        const V dfdw = vmul(g, vsub(vlit<V>(2.0), vmul(vlit<V>(4.0), f)));
         const V anti = vmul(vmul(vmul(K.one_m_A, d), vmul(pq, iMbar)), vmul(cross, rr));
         const V R = vfma(K.sigma, lap, vmul(K.dx2, vsub(anti, vfma(K.H, dfdw, vmul(dG, dp)))));
         sD[ry * RX + rx] = vmask(vmul(R, vrcp(Kc)), glo, ghi);
@@ -209,7 +209,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 #pragma unroll
         for (int k = 0; k < 4; ++k) t1[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
         const Q cL = sC[hL], cR = sC[hR];
-        face_flux<V, false, AI>(K, vmul(K.half, SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
+        face_flux<V, false, AI>(K, vmul(vlit<V>(0.5), SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
                             vadd(sD[rL], sD[rL + 1]), n, t1, t1, Fc, Fd);
     };
     // y faces above the two rows of the pair at hL: lanes (y+1/2, y+3/2)
@@ -230,7 +230,7 @@ step2d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         for (int k = 0; k < 4; ++k) t1[k] = vpair(DP[k].x + DP[k].y, DP[k].y + DN[k].x);
         const Q cP_ = sC[hL], cN_ = sC[hN];
         const V dP = sD[rL], dN = sD[rL + RX];
-        const V f = vmul(K.half, vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
+        const V f = vmul(vlit<V>(0.5), vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
         const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
         const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
         face_flux<V, false, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t1, Fc, Fd);

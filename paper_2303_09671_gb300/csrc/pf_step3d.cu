@@ -47,12 +47,13 @@ struct PTile {
     static constexpr int NH = HW * HYP;
     static constexpr int RW = TX + 2, NR = RW * HYP;    // halo-1 ring (all pair rows)
     // Row pitch of the plane arrays (measured: an odd pitch TX + 5 and a
-    // 128-byte-aligned pitch TX + 8 were both slower than the dense TX + 4).
+    // 128-byte-aligned pitch TX + 8 were both slower than the dense TX + 4,
+    // the latter also with the threads' own records 128-byte aligned: 8.6 %).
     static constexpr int HX = HW, RX = HX;
     static constexpr int OQ = 0, OV = 0, OD = 0, OF = 0;    // base shifts (elements)
     static constexpr int HP = HX * HYP, RP = HP;            // plane stride
     static constexpr int FXP = TX + 1;                      // x-face row pitch
-    static constexpr int NHP = (NH + 15) / 16 * 16;         // staging field stride (128-byte multiple)
+    static constexpr int NHP = (NH + 15) / 16 * 16;         // staging lane-plane stride
     static constexpr int JH = (NH + NT - 1) / NT;
     static constexpr size_t OFF_A = 0;                                   // {phi, Y}, 4 planes
     static constexpr size_t OFF_B = OFF_A + sizeof(Q) * 4 * HP;          // {mu_s, mu_l}, 4 planes
@@ -61,8 +62,8 @@ struct PTile {
     static constexpr size_t OFF_D = OFF_P + sizeof(V) * 3 * HP;          // dx^2 phidot, 2 planes
     static constexpr size_t OFF_FX = OFF_D + sizeof(V) * 2 * RP;         // x faces {F_c, F_d}
     static constexpr size_t OFF_FY = OFF_FX + sizeof(Q) * (TYP * FXP);       // upper y face {F_c, F_d}
-    static constexpr size_t OFF_R = OFF_FY + sizeof(V) * (TYP + 1) * TX;     // next plane: phi, c, d
-    static constexpr size_t OFF_O = OFF_R + sizeof(V) * 3 * NHP;             // own c, d, c_lo
+    static constexpr size_t OFF_R = OFF_FY + sizeof(V) * (TYP + 1) * TX;     // next plane: phi, c, d per lane
+    static constexpr size_t OFF_O = OFF_R + sizeof(V) * 3 * NHP;             // own c, d, c_lo per lane
     static constexpr size_t BYTES = OFF_O + sizeof(V) * 3 * NT;
     static constexpr int NB = NR - NT;   // ring cells besides the threads' own pairs
     static_assert(NB == 2 * RW + 2 * TYP && NB <= NT, "ring = own pairs + border");
@@ -156,8 +157,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 
     // ---- A: plane z -> staging (asynchronous copies; ghosts written directly).
     // The thread that copies a pair cell is the one that converts it.
-    T* sR = reinterpret_cast<T*>(smem + L::OFF_R);   // [field][h][lane]
-    T* sO = reinterpret_cast<T*>(smem + L::OFF_O);   // [field][tid][lane]
+    // lane-planar: consecutive threads copy to consecutive words (no bank conflicts)
+    T* sR = reinterpret_cast<T*>(smem + L::OFF_R);   // [field][lane][h]
+    T* sO = reinterpret_cast<T*>(smem + L::OFF_O);   // [field][lane][tid]
     auto fetch_plane = [&](int z) {
         const int mz = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]);
 #pragma unroll
@@ -166,7 +168,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             if ((j + 1) * NT > NH && h >= NH) break;
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                T* dst = sR + 2 * h + l;
+                T* dst = sR + l * NHP + h;
                 if (mz >= 0 && hoff[j][l] >= 0) {
                     const long long gi = (long long)mz * sz + hoff[j][l];
                     cp_async(dst, phi_in + gi);
@@ -182,16 +184,16 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
     auto fetch_own = [&](int z) {
         const long long gi = (long long)z * sz + own_xy;
-        T* dst = sO + 2 * tid;
+        T* dst = sO + tid;
         if (in_lo) {
             cp_async(dst, c_in + gi);
             cp_async(dst + 2 * NT, d_in + gi);
             if (clo_in != nullptr) cp_async(dst + 4 * NT, clo_in + gi);
         }
         if (in_hi) {
-            cp_async(dst + 1, c_in + gi + nx);
-            cp_async(dst + 1 + 2 * NT, d_in + gi + nx);
-            if (clo_in != nullptr) cp_async(dst + 1 + 4 * NT, clo_in + gi + nx);
+            cp_async(dst + NT, c_in + gi + nx);
+            cp_async(dst + 3 * NT, d_in + gi + nx);
+            if (clo_in != nullptr) cp_async(dst + 5 * NT, clo_in + gi + nx);
         }
     };
     // staged plane z into the rings
@@ -200,15 +202,16 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         Q* B = sB + (z & 3) * HP;
         Q* C = sC + slot3(z) * HP;
         V* P = sP + slot3(z) * HP;
-        const V* R = reinterpret_cast<const V*>(sR);
 #pragma unroll
         for (int j = 0; j < L::JH; ++j) {
             const int hl = tid + j * NT;
             if ((j + 1) * NT > NH && hl >= NH) break;
-            const V f = R[hl], c = R[NHP + hl], d = R[2 * NHP + hl];
+            const V f = vpair(sR[hl], sR[NHP + hl]);
+            const V c = vpair(sR[2 * NHP + hl], sR[3 * NHP + hl]);
+            const V d = vpair(sR[4 * NHP + hl], sR[5 * NHP + hl]);
             const int h = hring[j];
             const V p = vp_of<AI>(K, f);
-            const V cs = vfma(vsub(K.one, p), d, c);
+            const V cs = vfma(vsub(vlit<V>(1.0), p), d, c);
             const V cl = vsub(c, vmul(p, d));
             const V mus = vsub(vlog(cs), K.log_ke);
             const V mul = vlog(cl);
@@ -247,10 +250,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
                 const V EXY = vpair(XS.y + XP.y, XP.x + XN.x);
                 const V EZY = vpair(ZS.y + ZP.y, ZP.x + ZN.x);
                 const V EXZ = vadd(vadd(PM[h - 1], PM[h + 1]), vadd(PP[h - 1], PP[h + 1]));
-                lap = vsub(vfma(K.third, vadd(vadd(XP, ZP), YF), vmul(K.sixth, vadd(vadd(EXY, EZY), EXZ))),
-                           vmul(K.four, f));
+                lap = vsub(vfma(vlit<V>((1.0 / 3)), vadd(vadd(XP, ZP), YF), vmul(vlit<V>((1.0 / 6)), vadd(vadd(EXY, EZY), EXZ))),
+                           vmul(vlit<V>(4.0), f));
             } else {
-                lap = vsub(vadd(vadd(XP, ZP), YF), vmul(K.six, f));
+                lap = vsub(vadd(vadd(XP, ZP), YF), vmul(vlit<V>(6.0), f));
             }
             const Q cc = C0[h], bc = B0[h];
             const Q bxm = B0[h - 1], bxp = B0[h + 1], bS = B0[hS], bN = B0[hN], bzm = BM[h], bzp = BP[h];
@@ -260,7 +263,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V lx = vsub(bxp.b, bxm.b), ly = vpair(bc.b.y - bS.b.y, bN.b.x - bc.b.x), lz = vsub(bzp.b, bzm.b);
             const V cs = cc.a, cl = cc.b, mus = bc.a, mul = bc.b;
             const V p = vp_of<AI>(K, f), dp = vdp_of<AI>(K, f);
-            const V omp = vsub(K.one, p);
+            const V omp = vsub(vlit<V>(1.0), p);
             const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
             const V bMl = vmul(K.b, Ml);
             const V Msq = vmul(Ms, omp);
@@ -278,11 +281,11 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V theta = vpair(th_s, th_s);
             const V dmu = vsub(mus, mul);
             // D = [M_s (1-p)(1 - A(1-p)) + A b M_l p^2] / Mbar
-            const V Dd = vmul(vfma(Msq, vsub(K.one, vmul(K.A, omp)), vmul(vmul(K.A, bMl), vmul(p, p))), iMbar);
+            const V Dd = vmul(vfma(Msq, vsub(vlit<V>(1.0), vmul(K.A, omp)), vmul(vmul(K.A, bMl), vmul(p, p))), iMbar);
             // DeltaG = c_s (mu_s - mu_l) - d - (1-k_e) theta - D d (mu_s - mu_l)
             const V dG = vsub(vsub(vmul(cs, dmu), d), vfma(K.one_m_ke, theta, vmul(vmul(Dd, d), dmu)));
-            const V g = vmul(f, vsub(K.one, f));
-            const V dfdw = vmul(g, vsub(K.two, vmul(K.four, f)));
+            const V g = vmul(f, vsub(vlit<V>(1.0), f));
+            const V dfdw = vmul(g, vsub(vlit<V>(2.0), vmul(vlit<V>(4.0), f)));
             const V anti = vmul(vmul(vmul(K.one_m_A, d), vmul(pq, iMbar)), vmul(cross, rr));
             const V R = vfma(K.sigma, lap, vmul(K.dx2, vsub(anti, vfma(K.H, dfdw, vmul(dG, dp)))));
             pd = vmask(vmul(R, vrcp(Kc)), (dsc >> 12) & 1, (dsc >> 13) & 1);
@@ -324,7 +327,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         t2[2] = vsub(vadd(bPL.a, bPR.a), vadd(bML.a, bMR.a));
         t2[3] = vsub(vadd(bPL.b, bPR.b), vadd(bML.b, bMR.b));
         const Q cL = C0[hL], cR = C0[hR];
-        face_flux<V, true, AI>(K, vmul(K.half, SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
+        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
                   vadd(D0[rL], D0[rL + 1]), n, t1, t2, Fc, Fd);
     };
     // y faces above the two rows of the pair at hL: lanes (y+1/2, y+3/2)
@@ -359,7 +362,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         for (int k = 0; k < 4; ++k) t2[k] = vpair(EP[k].x + EP[k].y, EP[k].y + EN[k].x);
         const Q cP_ = C0[hL], cN_ = C0[hN];
         const V dP = D0[rL], dN = D0[rL + RX];
-        const V f = vmul(K.half, vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
+        const V f = vmul(vlit<V>(0.5), vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
         const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
         const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
         face_flux<V, true, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
@@ -395,7 +398,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             for (int k = 0; k < 4; ++k) t2[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
         }
         const Q c0 = C0[h], c1 = C1[h];
-        face_flux<V, true, AI>(K, vmul(K.half, vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
+        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
                   vadd(D0[r], D1[r]), n, t1, t2, Fc, Fd);
     };
     auto z_noflux = [&](int z) {
@@ -432,7 +435,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     __syncthreads();   // the loop's first store reuses the {c_s, c_l} slot of z0-1
 
     // fluxes of the plane being updated, carried from its faces phase to its update
-    V fxc, fxd, fyc, fyd, fzc, fzd;
+    V fxc = vlit<V>(0.0), fxd = fxc, fyc = fxc, fyd = fxc, fzc = fxc, fzd = fxc;
     // update of plane k from its fluxes and the own-cell state staged in sO
     auto update = [&](int k) {
         const Q left = sFx[ty * FXP + tx];
@@ -440,15 +443,14 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const T bc_ = below.x, bd_ = below.y;
         const V dFc = vadd(vadd(vsub(fxc, left.a), vpair(fyc.x - bc_, fyc.y - fyc.x)), vsub(fzc, fzc_down));
         const V dFd = vadd(vadd(vsub(fxd, left.b), vpair(fyd.x - bd_, fyd.y - fyd.x)), vsub(fzd, fzd_down));
-        const V* O = reinterpret_cast<const V*>(sO);
-        const V c_k = O[tid], d_k = O[NT + tid];
+        const V c_k = vpair(sO[tid], sO[NT + tid]), d_k = vpair(sO[2 * NT + tid], sO[3 * NT + tid]);
         const V phi_new = vfma(K.dt_dx2, sD[(k & 1) * RP + own_r], sA[(k & 3) * HP + own_h].a);
         const V d_new = vfma(K.dt_dx2, dFd, d_k);
         const V dcv = vmul(K.dt_dx2, dFc);
         V c_new, lo_new;
         if (clo_in != nullptr) {
             // compensated (TwoSum) update of c = hi + lo
-            const V lo_k = O[2 * NT + tid];
+            const V lo_k = vpair(sO[4 * NT + tid], sO[5 * NT + tid]);
             const V s_ = vadd(c_k, dcv);
             const V bv = vsub(s_, c_k);
             const V err = vadd(vsub(c_k, vsub(s_, bv)), vsub(dcv, bv));
