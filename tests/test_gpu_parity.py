@@ -146,6 +146,19 @@ def test_fp64_3d_dirichlet_mixed():
     assert_fields(st, g, TOL64, pr)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_generic_cross_check_kernel(dim, monkeypatch):
+    """PF_GENERIC=1 at pf_create runs 2D and 3D through the generic
+    one-cell-per-thread kernel (the cross-check of the paired kernels); it
+    matches the oracle at the same bar."""
+    monkeypatch.setenv("PF_GENERIC", "1")
+    n = (45, 19) if dim == 2 else (37, 19, 13)
+    bc = ("noflux", "periodic") if dim == 2 else ("noflux", "periodic", "noflux")
+    pr, phi, cs, cl = wl.random_state(dim, n, dx=0.5, A=1.5, b=0.3, a=-0.3, seed=13, bc_lo=bc, bc_hi=bc)
+    st, g, _ = run_pair(pr, phi, cs, cl, 40)
+    assert_fields(st, g, TOL64, pr)
+
+
 def test_fp64_1d_pulled_front_shift():
     pr, phi, cs, cl = wl.pulled_front_1d(N=512, V=0.2, A=1.0, b=1.0)
     st, g, clock = run_pair(pr, phi, cs, cl, 600)
