@@ -116,7 +116,15 @@ typedef struct pf_handle pf_handle;
  * PF_EINVAL for: dim outside 1..3, n[a] < 3 on an active axis or != 1 on an
  * inactive one, one-sided periodicity, dx <= 0, k_e outside (0,1), b <= 0,
  * H, sigma, M_phi, D_s, D_l <= 0, a stencil that does not match dim,
- * shift with dim != 1, dt <= 0 or dt above pf_stable_dt. */
+ * shift with dim != 1, dt <= 0 or dt above pf_stable_dt.
+ *
+ * The device state is (phi, c = p c_s + (1-p) c_l, d = c_s - c_l) in two
+ * ping-pong copies; an FP32 state also keeps the low FP32 word of c, and in
+ * 1D that of phi, so that both accumulate without rounding drift.  Two
+ * environment variables, read here, select kernels for testing and tuning:
+ * PF_GENERIC=1 runs 2D and 3D through the one-cell-per-thread kernel instead
+ * of the paired two-lane kernels (a cross-check; same results to rounding),
+ * PF_ZCHUNK=<planes> fixes the z-chunk of the 3D kernel. */
 int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
               void* stream, pf_handle** out);
 
