@@ -17,6 +17,7 @@ from scipy.linalg import solve_banded
 import oracle
 from paper_2303_09671_gb300 import workloads as wl
 
+import bruteforce
 from continuum import ContinuumModel, X, Y
 from conftest import rel_err
 
@@ -435,3 +436,49 @@ def test_literal_form_agrees_with_conservative_form():
         b.step(10)
         errs.append(max(np.abs(a.cs - b.cs).max(), np.abs(a.cl - b.cl).max()))
     assert errs[1] < errs[0] / 2.5, errs
+
+
+# --------------------------------------------------- brute force on tiny grids
+
+BRUTE_CASES = [
+    (1, (7,), dict(A=0.4, b=0.3, a=-0.3), 0),
+    (1, (6,), dict(A=2.0, b=1.0, a=0.0, bc_lo=("noflux",), bc_hi=("dirichlet",), G_theta=0.05, x0=1.0,
+                   v_pull=0.1), 40),
+    (2, (6, 5), dict(A=0.4, b=0.3, a=0.2, lap=9), 0),
+    (2, (5, 4), dict(A=1.5, b=0.3, a=0.0, lap=5, bc_lo=("noflux", "periodic"),
+                     bc_hi=("dirichlet", "periodic")), 0),
+    (3, (5, 4, 3), dict(A=0.4, b=0.3, a=-0.3, lap=19), 0),
+    (3, (4, 4, 4), dict(A=0.0, b=0.5, a=0.0, lap=7, bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3,
+                        interp="cubic", mobility="const"), 0),
+    (3, (4, 3, 5), dict(A=2.0, b=1.0, a=0.0, lap=19, bc_lo=("noflux", "periodic", "dirichlet"),
+                        bc_hi=("dirichlet", "periodic", "noflux"), G_theta=0.02), 0),
+]
+
+
+@pytest.mark.parametrize("dim,n,kw,step", BRUTE_CASES)
+def test_rates_match_brute_force_evaluator(dim, n, kw, step):
+    """The oracle's per-step rates (phidot, dc/dt, dd/dt) equal those of an
+    independent literal evaluator (tests/bruteforce.py: the equations of the
+    phase-field and concentration fluxes written out with Python loops over
+    cells and faces) to rounding, on 3-7 cells per axis, for every stencil,
+    boundary type, interpolation and mobility choice and a moving temperature.
+    The convergence pin above fixes the continuum limit; this one fixes the
+    discretisation itself (face means, one-sided normal and averaged transverse
+    face gradients, the stencils, ghost rules)."""
+    pr, phi, cs, cl = wl.random_state(dim, n, dx=0.5, seed=3 + step, **kw)
+    st = oracle.State(pr, phi, cs, cl, step=step)
+    got = st.rates()
+    want = bruteforce.rates(pr, phi, cs, cl, t=step * pr["dt"])
+    for name, a, b in zip(("phidot", "dc/dt", "dd/dt"), got, want):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (name, np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("plant", sorted(oracle.PLANT))
+def test_planted_mistakes_break_the_brute_force_pin(plant):
+    """Each planted mistake in the oracle moves its rates far from the literal
+    evaluator's, so the agreement above is not a coincidence of the state."""
+    pr, phi, cs, cl = wl.random_state(2, (6, 5), dx=0.5, seed=3, A=0.4, b=0.3, a=0.2, lap=9)
+    want = bruteforce.rates(pr, phi, cs, cl)
+    got = oracle.State(dict(pr, plant=plant), phi, cs, cl).rates()
+    err = max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(got, want))
+    assert err > 1e-6, (plant, err)
