@@ -329,6 +329,19 @@ def run_adjoint(args):
            "wall_ratio": adj_wall / fwd_wall,
            "k_forward_vs_adjoint_max_abs": float(np.abs(fwd["k_v"] - adj["k"]).max()),
            "loss": adj["loss"], "grad": [float(g) for g in adj["grad"]]}
+    if args.calibrate > 0:
+        # Adam on log(M_phi, A, b) towards the target curve, one pf_adjoint per iteration
+        t0 = time.perf_counter()
+        hist, err = [], None
+        try:
+            theta, hist = pf.calibrate(prs[0], lengths, vs, *f32, K, kt, iters=args.calibrate, lr=0.02,
+                                       precision="fp32", dt=dts)
+        except pf.PFError as e:   # a parameter set on which the run does not stay finite
+            theta, err = None, str(e)
+        out["calibration"] = {"iters": args.calibrate, "lr": 0.02, "wall_s": time.perf_counter() - t0,
+                              "loss_first": hist[0] if hist else None, "loss_last": hist[-1] if hist else None,
+                              "loss_min": min(hist) if hist else None, "params": theta, "error": err,
+                              "start": {k: prs[0][k] for k in pf.ADJ_PARAMS}}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -416,6 +429,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--calibrate", type=int, default=0,
+                    help="adjoint workload: Adam iterations of the k(V) calibration after the timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sphere3d",
                     choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d"])
