@@ -477,7 +477,7 @@ struct BatchRun {
         a.min_travel = D.min_travel;
         const pf_params& P = D.params;
         Consts<T>& C = a.C;
-        memset(&C, 0, sizeof(C));
+        C = Consts<T>{};   // every member zero (Dual members by their constructor)
         C.dim = 1; C.interp = P.interp; C.lap = 3; C.mobility = P.mobility_mode;
         C.dx = T(D.dx); C.inv_dx = T(1.0 / D.dx); C.inv_2dx = T(0.5 / D.dx); C.inv_dx2 = T(1.0 / (D.dx * D.dx));
         C.H = T(P.H); C.sigma = T(P.sigma); C.inv_Mphi = T(1.0 / P.M_phi); C.D_s = T(P.D_s); C.D_l = T(P.D_l);
