@@ -70,16 +70,23 @@ def shape_a(phi, r, b, a=0.0, interp="quintic"):
     return (r - b) * p * (1.0 - p) / (r * (1.0 - p) + b * p)
 
 
-def _half_integral(f, side):
-    """int_0^{+-inf} f(eta) d eta (side = +1 or -1)."""
-    val, _ = integrate.quad(f, 0.0, side * ETA_MAX, limit=400, epsabs=1e-14, epsrel=1e-12)
-    return val
+def _half_integral(g, side):
+    """int_0^{+-inf} g(phi_0(eta)) d eta (side = +1 or -1; for -1 the integral
+    runs from 0 down to -inf), taken over phi: d phi_0 / d eta =
+    -sqrt(2) phi (1 - phi), so eta in (0, +inf) is phi in (0, 1/2) and eta in
+    (-inf, 0) is phi in (1/2, 1), with the weight 1 / (sqrt 2 phi (1 - phi)).
+    The integrands here vanish at the ends at least like phi^2 (1 - phi)^2, so
+    the integral over phi is of a smooth function on a finite interval."""
+    lo, hi = (0.0, 0.5) if side > 0 else (0.5, 1.0)
+    val, _ = integrate.quad(lambda ph: g(ph) / (math.sqrt(2.0) * ph * (1.0 - ph)), lo, hi,
+                            limit=400, epsabs=1e-14, epsrel=1e-12)
+    return val if side > 0 else -val
 
 
 def G_pm(r, b, a=0.0, interp="quintic"):
     """(G^-, G^+) of Eq. integral3, in units of W (M_l factored out)."""
-    gp = _half_integral(lambda e: inv_qn(phi0(e), r, b, a, interp) - 1.0, +1)
-    gm = _half_integral(lambda e: inv_qn(phi0(e), r, b, a, interp) - 1.0 / r, -1)
+    gp = _half_integral(lambda ph: inv_qn(ph, r, b, a, interp) - 1.0, +1)
+    gm = _half_integral(lambda ph: inv_qn(ph, r, b, a, interp) - 1.0 / r, -1)
     return gm, gp
 
 
@@ -134,8 +141,8 @@ def F_pm(r, b, A, a=0.0, interp="quintic"):
     """(F^-, F^+) of Eq. integral1, in units of W."""
     lim_p = p_tilde(0.0, r, b, A, a, interp)   # liquid side, phi -> 0
     lim_m = p_tilde(1.0, r, b, A, a, interp)   # solid side, phi -> 1
-    fp = _half_integral(lambda e: p_tilde(phi0(e), r, b, A, a, interp) - lim_p, +1)
-    fm = _half_integral(lambda e: p_tilde(phi0(e), r, b, A, a, interp) - lim_m, -1)
+    fp = _half_integral(lambda ph: p_tilde(ph, r, b, A, a, interp) - lim_p, +1)
+    fm = _half_integral(lambda ph: p_tilde(ph, r, b, A, a, interp) - lim_m, -1)
     return fm, fp
 
 
