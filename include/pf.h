@@ -247,22 +247,33 @@ int pf_run_batch(const pf_batch_desc* desc, pf_batch_result* res, void* stream);
  * For every instance of `batch` (same meaning as for pf_run_batch; the
  * k_v-convergence fields are ignored) the run takes exactly `nsteps` steps
  * and evaluates k_i = c_inf / max_x c, c = p c_s + (1-p) c_l, at the end.
- * The derivatives dk_i/dtheta are exact derivatives of the discrete run
- * (tangent-linear: the state is carried as value + derivative along one
- * parameter, one CTA per instance and parameter, all concurrent); at the
- * maximum the derivative of the maximising cell is taken (a subgradient where
- * two cells tie).  With k_target given, the loss is
+ * The derivatives dk_i/dtheta are exact derivatives of the discrete run; at
+ * the maximum the derivative of the maximising cell is taken (a subgradient
+ * where two cells tie).  Two ways to the same numbers:
+ *   PF_ADJ_TANGENT  tangent-linear: the state is carried as value + derivative
+ *                   along one parameter, one CTA per instance and parameter,
+ *                   all concurrent;
+ *   PF_ADJ_REVERSE  reverse sweep: the forward run stores its state every
+ *                   checkpoint_every steps (0: ceil(sqrt(nsteps)), at most 1024);
+ *                   each segment is then re-run recording every step and swept
+ *                   backwards with the adjoint of the fused step, from
+ *                   d k_i / d c at the maximum, one CTA per instance.  The cost
+ *                   does not grow with the number of parameters.
+ * With k_target given, the loss is
  *   L = sum_i (k_i - k_target_i)^2,  dL/dtheta = sum_i 2 (k_i - k_target_i) dk_i/dtheta.
  * batch.params.precision selects FP32 or FP64 arithmetic for value and
  * derivative; instances hold at most 4096 (FP32) or 2048 (FP64) cells.
  * ------------------------------------------------------------------------ */
 enum { PF_ADJ_MPHI = 1, PF_ADJ_A = 2, PF_ADJ_B = 4 };
+enum { PF_ADJ_TANGENT = 0, PF_ADJ_REVERSE = 1 };
 
 typedef struct {
     pf_batch_desc batch;      /* instances, initial fields, shared parameters */
     int64_t nsteps;           /* steps per instance (> 0) */
     int wrt;                  /* parameters to differentiate: PF_ADJ_* bits (non-zero) */
     const double* k_target;   /* per instance, host; NULL: loss and grad are 0 */
+    int mode;                 /* PF_ADJ_TANGENT or PF_ADJ_REVERSE */
+    int checkpoint_every;     /* PF_ADJ_REVERSE: steps between stored states (0: automatic) */
 } pf_adjoint_desc;
 
 typedef struct {

@@ -63,6 +63,9 @@ struct BatchArgs {
     int energy_slots;               // records per instance in `energy`
     double* energy;                 // [instance][slot] F_h records (device)
     double dir_phi;                 // hot-end ghost phi, for the gradient energy
+    T* rec;                         // if set: the state before every step of the launch,
+                                    // [instance block of 3 rec_steps n][step][phi|c|d][n]
+    long long rec_steps;
 };
 
 template <typename T>
@@ -135,6 +138,14 @@ batch_kernel(BatchArgs<T> a) {
     for (int it = 0; it < a.nsteps; ++it) {
         const double t = (double)step * a.dt[inst];
         const T theta0 = T(a.theta_ref + a.G_theta * (a.x0 + v * t - (double)shifts * (double)C.dx));
+        if (a.rec != nullptr) {   // the pre-step state, for a reverse sweep
+            T* r = a.rec + 3 * a.rec_steps * off + (long long)it * 3 * n;
+            for (int i = tid; i < n; i += NT) {
+                r[i] = sPhi[i];
+                r[n + i] = sC[i];
+                r[2 * n + i] = sD[i];
+            }
+        }
         // P1: diffusion potentials
         for (int i = tid; i < n; i += NT) {
             T p, cs, cl;
@@ -448,6 +459,8 @@ struct BatchRun {
     std::vector<int> rep_dir;   // tangent runs: seeded parameter of each instance
     double* energy = nullptr;   // F_h records [instance][slot] (device), or null
     int energy_slots = 0;
+    T* rec = nullptr;           // reverse sweeps: per-step state record (not owned)
+    long long rec_steps = 0;
     cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
     int64_t launches = 0;
 
@@ -496,6 +509,8 @@ struct BatchRun {
         a.energy_slots = energy_slots;
         a.energy = energy;
         a.dir_phi = D.bc.dir_phi;
+        a.rec = rec;
+        a.rec_steps = rec_steps;
         if constexpr (IsDual<T>::value) {
             // seed d/dtheta = 1 on the parameter of this group
             using VT = decltype(C.A.v);
@@ -1050,12 +1065,738 @@ static int run_adjoint_T(const pf_adjoint_desc& A, pf_adjoint_result* R, cudaStr
     return PF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Reverse sweep (pf_adjoint, PF_ADJ_REVERSE): the adjoint of one fused 1D step
+// of batch_kernel, applied backwards over recorded states.  lambda = dk/du for
+// the state u = (phi, c, d) of one instance; the parameter derivatives collect
+// dk/d(1/M_phi), dk/dA, dk/db from every use inside the step.
+
+// p''(phi) (d/dphi of dp_of)
+template <typename T>
+__device__ __forceinline__ T d2p_of(const Consts<T>& C, T f) {
+    const T g = f * (T(1) - f);
+    const T d2h = C.dh1 + f * (T(2) * C.dh2 + f * (T(3) * C.dh3 + f * (T(4) * C.dh4)));
+    const T s = T(1) - T(2) * f;
+    const T dw = T(2) * g * s;
+    return d2h + C.a * (T(2) * dw + (f - T(0.5)) * T(2) * (s * s - T(2) * g));
+}
+
+// adjoints of the inputs of face1 (and of A, b) from those of its outputs (gc, gd)
+template <typename T>
+struct FaceAdj {
+    T f, cs, cl, pd;          // of each of the two cells' phi, c_s, c_l, phidot (half the face's)
+    T nphi, nY, nS, nL;       // of the normal differences
+    T A, b;                   // of the parameters
+};
+
+template <typename T>
+__device__ void face1_rev(const Consts<T>& C, T fL, T fR, T csL, T csR, T clL, T clR, T pdL, T pdR,
+                          T nphi, T nY, T nS, T nL, T gc, T gd, FaceAdj<T>& o) {
+    // forward values (as face1)
+    const T f = T(0.5) * (fL + fR);
+    const T cs = T(0.5) * (csL + csR), cl = T(0.5) * (clL + clR);
+    const T d = cs - cl;
+    const T pdot = T(0.5) * (pdL + pdR);
+    const T p = p_of(C, f);
+    const T omp = T(1) - p;
+    const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
+    const T bMl = C.b * Ml;
+    const T iM = T(1) / (Ms * omp + bMl * p);
+    const T g2 = C.delta2;
+    const T r = T(1) / (nphi * nphi + g2);
+    const T Ts = Ms * nS * g2;
+    const T Tl = Ml * nL * g2;
+    const T at = C.one_m_A * d * pdot * nphi;
+    const T u = C.b * p + omp;
+    const T q = Ms * Ml * u * iM;
+    const T ppo = p * omp;
+    const T afn = (Ms - bMl) * ppo * iM;
+    const T Ssum = q * nphi * nphi * nY + p * Ts + omp * Tl + at * afn;
+    // reverse
+    const T lr = gc * Ssum + gd * (Ts - Tl + at);
+    const T lS = gc * r;
+    const T lTs = lS * p + gd * r;
+    const T lTl = lS * omp - gd * r;
+    const T lat = lS * afn + gd * r;
+    const T lq = lS * nphi * nphi * nY;
+    T lnphi = lS * q * T(2) * nphi * nY;
+    const T lnY = lS * q * nphi * nphi;
+    T lp = lS * (Ts - Tl);
+    const T lafn = lS * at;
+    T lMs = lafn * ppo * iM;
+    T lbMl = -lafn * ppo * iM;
+    lp += lafn * (Ms - bMl) * (omp - p) * iM;
+    T liM = lafn * (Ms - bMl) * ppo;
+    lMs += lq * Ml * u * iM;
+    T lMl = lq * Ms * u * iM;
+    const T lu = lq * Ms * Ml * iM;
+    liM += lq * Ms * Ml * u;
+    lp += lu * (C.b - T(1));
+    T lb = lu * p;
+    const T ld = lat * C.one_m_A * pdot * nphi;
+    const T lpdot = lat * C.one_m_A * d * nphi;
+    lnphi += lat * C.one_m_A * d * pdot;
+    const T lA = -lat * d * pdot * nphi;
+    lMs += lTs * nS * g2;
+    const T lnS = lTs * Ms * g2;
+    lMl += lTl * nL * g2;
+    const T lnL = lTl * Ml * g2;
+    lnphi += lr * (-r * r) * (T(2) * nphi);
+    const T lMb = -liM * iM * iM;
+    lMs += lMb * omp;
+    lp += lMb * (bMl - Ms);
+    lbMl += lMb * p;
+    lMl += lbMl * C.b;
+    lb += lbMl * Ml;
+    T lcs = lMs * C.Ms_c + ld;
+    T lcl = lMl * C.Ml_c - ld;
+    const T lf = lp * dp_of(C, f);
+    o.f = T(0.5) * lf;
+    o.cs = T(0.5) * lcs;
+    o.cl = T(0.5) * lcl;
+    o.pd = T(0.5) * lpdot;
+    o.nphi = lnphi;
+    o.nY = lnY;
+    o.nS = lnS;
+    o.nL = lnL;
+    o.A = lA;
+    o.b = lb;
+}
+
+template <typename T>
+struct RevArgs {
+    const T* rec;            // recorded pre-step states of the segment (batch_kernel layout)
+    long long rec_steps;
+    T* lphi;                 // adjoint state, packed like the value state
+    T* lc;
+    T* ld;
+    double* grad;            // [instance][3]: d k_i / d(1/M_phi, A, b), accumulated
+    const BatchState* st0;   // per instance at the segment start (off, n, step, shifts)
+    const double* v;
+    const double* dt;
+    int nsteps;              // steps of this segment (<= RMAX_SEG)
+    Consts<T> C;
+    double theta_ref, G_theta, x0;
+    T gphi, gcs, gcl, gmus, gmul;   // Dirichlet (hot end) ghost
+};
+
+constexpr int RMAX_SEG = 1024;
+
+template <typename T, int NT, int RJ>
+__global__ void __launch_bounds__(NT, 1) reverse_kernel(RevArgs<T> a) {
+    const int inst = blockIdx.x;
+    const BatchState S0 = a.st0[inst];
+    const int n = S0.n;
+    const long long off = S0.off;
+    const Consts<T>& C = a.C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sF = reinterpret_cast<T*>(smem);   // phi
+    T* sCs = sF + n;                      // c_s
+    T* sCl = sCs + n;                     // c_l
+    T* sMs = sCl + n;                     // mu_s
+    T* sMl = sMs + n;                     // mu_l
+    T* sPd = sMl + n;                     // phidot
+    T* sLf = sPd + n;                     // adjoints of phi, c, d
+    T* sLc = sLf + n;
+    T* sLd = sLc + n;
+    T* sXl = sLd + n;                     // per cell: adjoints of its rate's lap, d_x phi, d_x mu_s, d_x mu_l
+    T* sXg = sXl + n;
+    T* sXs = sXg + n;
+    T* sXm = sXs + n;
+    __shared__ int nsh[RMAX_SEG];         // window shifts that followed each step
+    __shared__ double th0[RMAX_SEG];      // theta0 of each step
+    __shared__ double red[NT / 32];
+    const int tid = threadIdx.x;
+    const double v = a.v[inst];
+    const double dtd = a.dt[inst];
+    const T dt = T(dtd);
+    const T dtdx = dt * C.inv_dx;
+    if (tid == 0) {   // replay the clock of batch_kernel over the segment
+        long long step = S0.step, shifts = S0.shifts;
+        for (int it = 0; it < a.nsteps; ++it) {
+            th0[it] = a.theta_ref + a.G_theta * (a.x0 + v * ((double)step * dtd) - (double)shifts * (double)C.dx);
+            step += 1;
+            const double tn = (double)step * dtd;
+            int k = 0;
+            while (v * tn >= (double)(shifts + 1) * (double)C.dx) {
+                shifts += 1;
+                k += 1;
+            }
+            nsh[it] = k;
+        }
+    }
+    for (int i = tid; i < n; i += NT) {
+        sLf[i] = a.lphi[off + i];
+        sLc[i] = a.lc[off + i];
+        sLd[i] = a.ld[off + i];
+    }
+    __syncthreads();
+    double gM = 0.0, gA = 0.0, gB = 0.0;
+    const T pg = p_of(C, a.gphi);
+    const T Yg = a.gmul + pg * (a.gmus - a.gmul);
+
+    for (int it = a.nsteps - 1; it >= 0; --it) {
+        // the window shifts after this step, undone: lambda moves one cell back
+        for (int k = 0; k < nsh[it]; ++k) {
+            T tf[RJ], tc[RJ], td[RJ];
+#pragma unroll
+            for (int j = 0; j < RJ; ++j) {
+                const int i = tid + j * NT;
+                if (i >= n) break;
+                tf[j] = i > 0 ? sLf[i - 1] : T(0);
+                tc[j] = i > 0 ? sLc[i - 1] : T(0);
+                td[j] = i > 0 ? sLd[i - 1] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < RJ; ++j) {
+                const int i = tid + j * NT;
+                if (i >= n) break;
+                sLf[i] = tf[j];
+                sLc[i] = tc[j];
+                sLd[i] = td[j];
+            }
+            __syncthreads();
+        }
+        // forward values of the step from the recorded state
+        const T* r = a.rec + 3 * a.rec_steps * off + (long long)it * 3 * n;
+        T dval[RJ], pval[RJ];
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) {
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            const T f = r[i], c = r[n + i], d = r[2 * n + i];
+            const T p = p_of(C, f);
+            const T cs = c + (T(1) - p) * d, cl = c - p * d;
+            sF[i] = f;
+            sCs[i] = cs;
+            sCl[i] = cl;
+            sMs[i] = flog(cs) - C.log_ke;
+            sMl[i] = flog(cl);
+            dval[j] = d;
+            pval[j] = p;
+        }
+        __syncthreads();
+        const T theta0 = T(th0[it]);
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) {   // phidot, as batch_kernel (Dirichlet hot end)
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            const int im = (i == 0) ? 0 : i - 1;
+            const bool last = i == n - 1;
+            const T fc = sF[i], fW = sF[im], fE = last ? a.gphi : sF[i + 1];
+            const T mWs = sMs[im], mWl = sMl[im];
+            const T mEs = last ? a.gmus : sMs[i + 1], mEl = last ? a.gmul : sMl[i + 1];
+            const T p = pval[j], cs = sCs[i], cl = sCl[i], mus = sMs[i], mul = sMl[i];
+            const T dp = dp_of(C, fc);
+            const T lap = (fW - T(2) * fc + fE) * C.inv_dx2;
+            const T gp = (fE - fW) * C.inv_2dx;
+            const T gs = (mEs - mWs) * C.inv_2dx;
+            const T gl = (mEl - mWl) * C.inv_2dx;
+            const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
+            const T bMl = C.b * Ml;
+            const T Msq = Ms * (T(1) - p);
+            const T iM = T(1) / (Msq + bMl * p);
+            const T d = cs - cl;
+            const T rr = T(1) / (gp * gp + C.delta2);
+            const T pq = p * (T(1) - p);
+            const T Kc = C.inv_Mphi + C.one_m_A * C.one_m_A * d * d * C.b * pq * rr * iM / (C.b * p + T(1) - p);
+            const T theta = theta0 - C.G_theta * ((T(i) + T(0.5)) * C.dx);
+            const T dmu = mus - mul;
+            const T Dd = (Msq * (T(1) - C.A * (T(1) - p)) + C.A * bMl * p * p) * iM;
+            const T dG = cs * dmu - d - C.one_m_ke * theta - Dd * d * dmu;
+            const T dfdw = T(2) * fc * (T(1) - fc) * (T(1) - T(2) * fc);
+            const T R = C.sigma * lap - C.H * dfdw - dG * dp +
+                        C.one_m_A * d * pq * iM * (Ms * gs - bMl * gl) * gp * rr;
+            sPd[i] = R / Kc;
+        }
+        __syncthreads();
+        // R1: the two faces of each cell, their parts that act on the cell
+        T aF[RJ], aCs[RJ], aCl[RJ], aMs[RJ], aMl[RJ], aP[RJ], aPd[RJ];
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) {
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            const T f0 = sF[i], cs0 = sCs[i], cl0 = sCl[i], ms0 = sMs[i], ml0 = sMl[i], pd0 = sPd[i];
+            const T p0 = pval[j];
+            const T Y0 = ml0 + p0 * (ms0 - ml0);
+            T lf = T(0), lcs = T(0), lcl = T(0), lms = T(0), lml = T(0), lY = T(0);
+            T lpd = dt * sLf[i];
+            FaceAdj<T> o;
+            if (i > 0) {   // face (i-1, i): this cell is its right side
+                const T fL = sF[i - 1], csL = sCs[i - 1], clL = sCl[i - 1], msL = sMs[i - 1], mlL = sMl[i - 1];
+                const T pL = p_of(C, fL);
+                const T YL = mlL + pL * (msL - mlL);
+                const T gc = dtdx * (sLc[i - 1] - sLc[i]), gd = dtdx * (sLd[i - 1] - sLd[i]);
+                face1_rev(C, fL, f0, csL, cs0, clL, cl0, sPd[i - 1], pd0, (f0 - fL) * C.inv_dx,
+                          (Y0 - YL) * C.inv_dx, (ms0 - msL) * C.inv_dx, (ml0 - mlL) * C.inv_dx, gc, gd, o);
+                lf += o.f + o.nphi * C.inv_dx;
+                lcs += o.cs;
+                lcl += o.cl;
+                lpd += o.pd;
+                lY += o.nY * C.inv_dx;
+                lms += o.nS * C.inv_dx;
+                lml += o.nL * C.inv_dx;
+            }
+            {              // face (i, i+1), or (n-1, ghost): this cell is its left side
+                const bool last = i == n - 1;
+                const T fR = last ? a.gphi : sF[i + 1];
+                const T csR = last ? a.gcs : sCs[i + 1], clR = last ? a.gcl : sCl[i + 1];
+                const T msR = last ? a.gmus : sMs[i + 1], mlR = last ? a.gmul : sMl[i + 1];
+                const T YR = last ? Yg : mlR + p_of(C, fR) * (msR - mlR);
+                const T pdR = last ? T(0) : sPd[i + 1];
+                const T gc = dtdx * (sLc[i] - (last ? T(0) : sLc[i + 1]));
+                const T gd = dtdx * (sLd[i] - (last ? T(0) : sLd[i + 1]));
+                face1_rev(C, f0, fR, cs0, csR, cl0, clR, pd0, pdR, (fR - f0) * C.inv_dx,
+                          (YR - Y0) * C.inv_dx, (msR - ms0) * C.inv_dx, (mlR - ml0) * C.inv_dx, gc, gd, o);
+                lf += o.f - o.nphi * C.inv_dx;
+                lcs += o.cs;
+                lcl += o.cl;
+                lpd += o.pd;
+                lY -= o.nY * C.inv_dx;
+                lms -= o.nS * C.inv_dx;
+                lml -= o.nL * C.inv_dx;
+                gA += (double)o.A;   // each face's parameter terms counted once, by its left cell
+                gB += (double)o.b;
+            }
+            // Y = mu_l + p (mu_s - mu_l)
+            lms += lY * p0;
+            lml += lY * (T(1) - p0);
+            aP[j] = lY * (ms0 - ml0);
+            aF[j] = lf;
+            aCs[j] = lcs;
+            aCl[j] = lcl;
+            aMs[j] = lms;
+            aMl[j] = lml;
+            aPd[j] = lpd;
+        }
+        // R2: the phase-field rate of each cell, backwards
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) {
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            const int im = (i == 0) ? 0 : i - 1;
+            const bool last = i == n - 1;
+            const T fc = sF[i], fW = sF[im], fE = last ? a.gphi : sF[i + 1];
+            const T mWs = sMs[im], mWl = sMl[im];
+            const T mEs = last ? a.gmus : sMs[i + 1], mEl = last ? a.gmul : sMl[i + 1];
+            const T p = pval[j], cs = sCs[i], cl = sCl[i], mus = sMs[i], mul = sMl[i];
+            const T dp = dp_of(C, fc);
+            const T lap = (fW - T(2) * fc + fE) * C.inv_dx2;
+            const T gp = (fE - fW) * C.inv_2dx;
+            const T gs = (mEs - mWs) * C.inv_2dx;
+            const T gl = (mEl - mWl) * C.inv_2dx;
+            const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
+            const T bMl = C.b * Ml;
+            const T omp = T(1) - p;
+            const T Msq = Ms * omp;
+            const T iM = T(1) / (Msq + bMl * p);
+            const T d = cs - cl;
+            const T rr = T(1) / (gp * gp + C.delta2);
+            const T pq = p * omp;
+            const T u = C.b * p + omp;
+            const T oA = C.one_m_A;
+            const T K2 = oA * oA * d * d * C.b * pq * rr * iM / u;
+            const T Kc = C.inv_Mphi + K2;
+            const T theta = theta0 - C.G_theta * ((T(i) + T(0.5)) * C.dx);
+            const T dmu = mus - mul;
+            const T Nv = Msq * (T(1) - C.A * omp) + C.A * bMl * p * p;
+            const T Dd = Nv * iM;
+            const T dG = cs * dmu - d - C.one_m_ke * theta - Dd * d * dmu;
+            const T W = Ms * gs - bMl * gl;
+            const T Xv = W * gp * rr;
+            const T pd = sPd[i];
+            const T lpd = aPd[j];
+            const T lR = lpd / Kc;
+            const T lKc = -lpd * pd / Kc;
+            const T llap = lR * C.sigma;
+            const T ldfdw = -lR * C.H;
+            const T ldG = -lR * dp;
+            const T ldp = -lR * dG;
+            // Z = (1-A) d pq iM X
+            T loA = lR * d * pq * iM * Xv;
+            T ld = lR * oA * pq * iM * Xv;
+            T lpq = lR * oA * d * iM * Xv;
+            T liM = lR * oA * d * pq * Xv;
+            const T lX = lR * oA * d * pq * iM;
+            const T lW = lX * gp * rr;
+            T lgp = lX * W * rr;
+            T lrr = lX * W * gp;
+            T lMs = lW * gs;
+            const T lgs = lW * Ms;
+            T lbMl = -lW * gl;
+            const T lgl = -lW * bMl;
+            // Kc = 1/M_phi + (1-A)^2 d^2 b pq rr iM / u
+            gM += (double)lKc;
+            loA += lKc * T(2) * oA * d * d * C.b * pq * rr * iM / u;
+            ld += lKc * oA * oA * T(2) * d * C.b * pq * rr * iM / u;
+            T lb = lKc * oA * oA * d * d * pq * rr * iM / u;
+            lpq += lKc * oA * oA * d * d * C.b * rr * iM / u;
+            lrr += lKc * oA * oA * d * d * C.b * pq * iM / u;
+            liM += lKc * oA * oA * d * d * C.b * pq * rr / u;
+            const T lu = -lKc * K2 / u;
+            T lp = lu * (C.b - T(1));
+            lb += lu * p;
+            // dG = cs dmu - d - (1-k_e) theta - Dd d dmu
+            T lcs = ldG * dmu;
+            const T ldmu = ldG * (cs - Dd * d);
+            ld += -ldG * (T(1) + Dd * dmu);
+            const T lDd = -ldG * d * dmu;
+            // Dd = Nv iM
+            const T lN = lDd * iM;
+            liM += lDd * Nv;
+            T lMsq = lN * (T(1) - C.A * omp);
+            gA += (double)(lN * (-Msq * omp + bMl * p * p));
+            lp += lN * (Msq * C.A + T(2) * C.A * bMl * p);
+            lbMl += lN * C.A * p * p;
+            // dmu, pq, rr, iM, Msq, bMl, Ms, Ml, d
+            const T lmus = ldmu, lmul = -ldmu;
+            lp += lpq * (T(1) - T(2) * p);
+            lgp += lrr * (-rr * rr) * (T(2) * gp);
+            const T lden = -liM * iM * iM;
+            lMsq += lden;
+            lbMl += lden * p;
+            lp += lden * bMl;
+            lMs += lMsq * omp;
+            lp -= lMsq * Ms;
+            T lMl = lbMl * C.b;
+            lb += lbMl * Ml;
+            lcs += lMs * C.Ms_c + ld;
+            T lcl = lMl * C.Ml_c - ld;
+            gA -= (double)loA;   // one_m_A = 1 - A
+            gB += (double)lb;
+            // phi of the cell itself: f_dw', p', the Laplacian's centre (and its own
+            // west neighbour at the mirrored cold end)
+            T lf = ldfdw * T(2) * (T(1) - T(6) * fc + T(6) * fc * fc) + ldp * d2p_of(C, fc)
+                   - T(2) * llap * C.inv_dx2;
+            T lms_self = lmus, lml_self = lmul;
+            if (i == 0) {
+                lf += llap * C.inv_dx2 - lgp * C.inv_2dx;
+                lms_self -= lgs * C.inv_2dx;
+                lml_self -= lgl * C.inv_2dx;
+            }
+            aF[j] += lf;
+            aCs[j] += lcs;
+            aCl[j] += lcl;
+            aMs[j] += lms_self;
+            aMl[j] += lml_self;
+            aP[j] += lp;
+            sXl[i] = llap;
+            sXg[i] = lgp;
+            sXs[i] = lgs;
+            sXm[i] = lgl;
+        }
+        __syncthreads();
+        // R3: the neighbours' rates, then the pointwise values, into the adjoint
+        // of the pre-step state (in place: R3 reads only its own cells' lambda)
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) {
+            const int i = tid + j * NT;
+            if (i >= n) break;
+            T lf = aF[j], lms = aMs[j], lml = aMl[j];
+            if (i > 0) {        // this cell is the east neighbour of cell i-1
+                lf += sXl[i - 1] * C.inv_dx2 + sXg[i - 1] * C.inv_2dx;
+                lms += sXs[i - 1] * C.inv_2dx;
+                lml += sXm[i - 1] * C.inv_2dx;
+            }
+            if (i < n - 1) {    // and the west neighbour of cell i+1
+                lf += sXl[i + 1] * C.inv_dx2 - sXg[i + 1] * C.inv_2dx;
+                lms -= sXs[i + 1] * C.inv_2dx;
+                lml -= sXm[i + 1] * C.inv_2dx;
+            }
+            const T cs = sCs[i], cl = sCl[i];
+            const T lcs = aCs[j] + lms / cs;
+            const T lcl = aCl[j] + lml / cl;
+            const T p = pval[j];
+            const T lp = aP[j] - dval[j] * (lcs + lcl);
+            sLf[i] = sLf[i] + lf + lp * dp_of(C, sF[i]);
+            sLc[i] = sLc[i] + lcs + lcl;
+            sLd[i] = sLd[i] + lcs * (T(1) - p) - lcl * p;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += NT) {
+        a.lphi[off + i] = sLf[i];
+        a.lc[off + i] = sLc[i];
+        a.ld[off + i] = sLd[i];
+    }
+    // parameter derivatives: block sums, one writer per instance
+    double vals[3] = {gM, gA, gB};
+    for (int q = 0; q < 3; ++q) {
+        double x = vals[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((tid & 31) == 0) red[tid >> 5] = x;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < NT / 32; ++w) tot += red[w];
+            a.grad[3 * inst + q] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// per instance: max_x c and the lowest maximising index
+template <typename V>
+__global__ void __launch_bounds__(256) value_cmax(const V* __restrict__ c, const BatchState* __restrict__ st,
+                                                  double* __restrict__ cmax, int* __restrict__ imax) {
+    const BatchState S = st[blockIdx.x];
+    double best = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
+        const double x = (double)c[S.off + i];
+        if (x > best || (x == best && i < bi)) {
+            best = x;
+            bi = i;
+        }
+    }
+    __shared__ double sb[256];
+    __shared__ int si[256];
+    sb[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            const double vb = sb[threadIdx.x + o];
+            const int ib = si[threadIdx.x + o];
+            if (vb > sb[threadIdx.x] || (vb == sb[threadIdx.x] && ib < si[threadIdx.x])) {
+                sb[threadIdx.x] = vb;
+                si[threadIdx.x] = ib;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        cmax[blockIdx.x] = sb[0];
+        imax[blockIdx.x] = si[0];
+    }
+}
+
+// lambda at the end of the run: d k_i / d c at the maximising cell, -c_inf / c_max^2
+template <typename V>
+__global__ void seed_lambda(V* __restrict__ lc, const BatchState* __restrict__ st, const double* __restrict__ cmax,
+                            const int* __restrict__ imax, double cinf, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // a run that went non-finite has no maximising cell: nothing is seeded (k is NaN)
+    if (i < N && imax[i] >= 0 && imax[i] < st[i].n) lc[st[i].off + imax[i]] = V(-cinf / (cmax[i] * cmax[i]));
+}
+
+template <typename V>
+struct RevKernel;
+template <>
+struct RevKernel<double> {
+    static constexpr int NT = 512, RJ = 4;   // up to 2048 cells
+};
+template <>
+struct RevKernel<float> {
+    static constexpr int NT = 512, RJ = 8;   // up to 4096 cells
+};
+
+template <typename V>
+static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R, cudaStream_t main, std::string& err) {
+    constexpr int NT = RevKernel<V>::NT, RJ = RevKernel<V>::RJ;
+    pf_batch_desc D = A.batch;
+    D.check_every = 0;   // a fixed number of steps
+    D.energy_every = 0;
+    const int N = D.n_instances;
+    BatchRun<V> B(D, main, err);
+    B.off.resize(N);
+    for (int i = 0; i < N; ++i) {
+        B.off[i] = B.total;
+        B.total += D.n[i];
+    }
+    if (!batch_time_steps(D, B.dt, err)) return PF_EINVAL;
+    int64_t nmax = 0;
+    for (int i = 0; i < N; ++i) nmax = std::max(nmax, (int64_t)D.n[i]);
+    const int64_t seg = std::min<int64_t>(
+        {A.checkpoint_every > 0 ? (int64_t)A.checkpoint_every
+                                : (int64_t)std::ceil(std::sqrt((double)A.nsteps)),
+         (int64_t)RMAX_SEG, A.nsteps});
+    const int64_t nseg = (A.nsteps + seg - 1) / seg;
+    const size_t fb = (size_t)B.total * sizeof(V);
+    V *scs = nullptr, *scl = nullptr, *ckp = nullptr, *ckc = nullptr, *ckd = nullptr, *rec = nullptr;
+    V *lphi = nullptr, *lc = nullptr, *ld = nullptr;
+    BatchState* ckst = nullptr;
+    double *grad = nullptr, *cmax = nullptr;
+    int* imax = nullptr;
+    auto free_tmp = [&] {
+        void* ptrs[] = {scs, scl, ckp, ckc, ckd, rec, lphi, lc, ld, ckst, grad, cmax, imax};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    };
+    cudaError_t e = cudaMalloc(&B.phi, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.c, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.d, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&B.st, N * sizeof(BatchState));
+    if (e == cudaSuccess) e = cudaMalloc(&B.dv, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&B.ddt, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&scs, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&scl, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&ckp, fb * nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&ckc, fb * nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&ckd, fb * nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&ckst, (size_t)N * nseg * sizeof(BatchState));
+    if (e == cudaSuccess) e = cudaMalloc(&rec, fb * 3 * seg);
+    if (e == cudaSuccess) e = cudaMalloc(&lphi, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&lc, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&ld, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&grad, 3 * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&cmax, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&imax, N * sizeof(int));
+    if (e != cudaSuccess) {
+        free_tmp();
+        cudaGetLastError();
+        err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return PF_ENOMEM;
+    }
+    std::vector<BatchState> hs(N);
+    for (int i = 0; i < N; ++i) hs[i] = BatchState{B.off[i], (int)D.n[i], 0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+    e = cudaMemcpyAsync(B.phi, D.phi0, fb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scs, D.cs0, fb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scl, D.cl0, fb, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.st, hs.data(), N * sizeof(BatchState), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.dv, D.v_pull, N * sizeof(double), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.ddt, B.dt.data(), N * sizeof(double), cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lphi, 0, fb, main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lc, 0, fb, main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ld, 0, fb, main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, 3 * N * sizeof(double), main);
+    if (e == cudaSuccess) {
+        batch_to_state<V><<<1216, 256, 0, main>>>(scs, scl, B.phi, B.c, B.d, B.total, D.params.interp, D.params.a);
+        e = cudaGetLastError();
+    }
+    size_t max_dyn = 0;
+    if (e == cudaSuccess) e = set_smem_limits<V>(&max_dyn);
+    const size_t rsmem = (size_t)13 * nmax * sizeof(V);
+    if (e == cudaSuccess) {
+        static DeviceSetup setup;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess && (dev < 0 || dev >= DeviceSetup::MAX_DEVICES)) e = cudaErrorInvalidDevice;
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> lock(setup.mu);
+            if (!setup.done[dev]) {
+                int optin = 0;
+                setup.err[dev] = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+                if (setup.err[dev] == cudaSuccess) setup.err[dev] = raise_smem(reverse_kernel<V, NT, RJ>, optin);
+                cudaFuncAttributes fa;
+                if (setup.err[dev] == cudaSuccess) setup.err[dev] = cudaFuncGetAttributes(&fa, reverse_kernel<V, NT, RJ>);
+                setup.value[dev] = setup.err[dev] == cudaSuccess ? (size_t)optin - fa.sharedSizeBytes : 0;
+                setup.done[dev] = true;
+            }
+            e = setup.err[dev];
+            if (e == cudaSuccess && rsmem > setup.value[dev]) {
+                free_tmp();
+                err = "longest instance does not fit in shared memory for the reverse sweep";
+                return PF_EINVAL;
+            }
+        }
+    }
+    if (e == cudaSuccess && (size_t)6 * nmax * sizeof(V) > max_dyn) {
+        free_tmp();
+        err = "longest instance does not fit in shared memory";
+        return PF_EINVAL;
+    }
+    const int cpt = D.cells_per_thread > 0 ? D.cells_per_thread : 8;
+    if (e == cudaSuccess) e = B.make_groups(cpt);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&B.t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&B.t1);
+    if (e == cudaSuccess) e = cudaEventRecord(B.t0, main);
+    // forward: the state (and clock) before every segment, then the segment
+    for (int64_t s = 0; s < nseg && e == cudaSuccess; ++s) {
+        const int64_t len = std::min(seg, A.nsteps - s * seg);
+        e = cudaMemcpyAsync(ckp + s * B.total, B.phi, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ckc + s * B.total, B.c, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ckd + s * B.total, B.d, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ckst + s * N, B.st, N * sizeof(BatchState), cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = B.issue((int)len);
+    }
+    if (e == cudaSuccess) {
+        value_cmax<V><<<N, 256, 0, main>>>(B.c, B.st, cmax, imax);
+        seed_lambda<V><<<(N + 255) / 256, 256, 0, main>>>(lc, B.st, cmax, imax, D.params.c_inf, N);
+        e = cudaGetLastError();
+    }
+    // backwards: re-run each segment recording every step, then sweep it
+    B.rec = rec;
+    B.rec_steps = seg;
+    for (int64_t s = nseg - 1; s >= 0 && e == cudaSuccess; --s) {
+        const int64_t len = std::min(seg, A.nsteps - s * seg);
+        e = cudaMemcpyAsync(B.phi, ckp + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.c, ckc + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.d, ckd + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(B.st, ckst + s * N, N * sizeof(BatchState), cudaMemcpyDeviceToDevice, main);
+        if (e == cudaSuccess) e = B.issue((int)len);
+        if (e == cudaSuccess) {
+            const BatchArgs<V> ba = B.args(B.groups[0], (int)len);
+            RevArgs<V> ra;
+            ra.rec = rec;
+            ra.rec_steps = seg;
+            ra.lphi = lphi;
+            ra.lc = lc;
+            ra.ld = ld;
+            ra.grad = grad;
+            ra.st0 = ckst + s * N;
+            ra.v = B.dv;
+            ra.dt = B.ddt;
+            ra.nsteps = (int)len;
+            ra.C = ba.C;
+            ra.theta_ref = ba.theta_ref;
+            ra.G_theta = ba.G_theta;
+            ra.x0 = ba.x0;
+            ra.gphi = ba.gphi;
+            ra.gcs = ba.gcs;
+            ra.gcl = ba.gcl;
+            ra.gmus = ba.gmus;
+            ra.gmul = ba.gmul;
+            reverse_kernel<V, NT, RJ><<<N, NT, rsmem, main>>>(ra);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(B.t1, main);
+    std::vector<double> hg(3 * N), hc(N);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hg.data(), grad, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, main);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cmax, N * sizeof(double), cudaMemcpyDeviceToHost, main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+    float ms = 0;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, B.t0, B.t1);
+    free_tmp();
+    if (e != cudaSuccess) {
+        err = std::string("reverse adjoint run: ") + cudaGetErrorString(e);
+        return PF_ECUDA;
+    }
+    const double cinf = D.params.c_inf, Mphi = D.params.M_phi;
+    R->loss = 0.0;
+    R->grad[0] = R->grad[1] = R->grad[2] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double k = cinf / hc[i];
+        if (R->k) R->k[i] = k;
+        // d k / d(1/M_phi) -> d k / d M_phi
+        const double all[3] = {hg[3 * i] * (-1.0 / (Mphi * Mphi)), hg[3 * i + 1], hg[3 * i + 2]};
+        double dk[3];
+        for (int j = 0; j < 3; ++j) dk[j] = ((A.wrt >> j) & 1) ? all[j] : 0.0;
+        if (R->dk)
+            for (int j = 0; j < 3; ++j) R->dk[3 * i + j] = dk[j];
+        if (A.k_target) {
+            const double res = k - A.k_target[i];
+            R->loss += res * res;
+            for (int j = 0; j < 3; ++j) R->grad[j] += 2.0 * res * dk[j];
+        }
+    }
+    R->gpu_ms = ms;
+    return PF_OK;
+}
+
 int run_adjoint(const pf_adjoint_desc* A, pf_adjoint_result* R, void* stream, std::string& err) {
     if (!A || !R) { err = "null argument"; return PF_EINVAL; }
     const pf_batch_desc& D = A->batch;
     const pf_params& P = D.params;
     if (A->nsteps <= 0 || A->nsteps > (int64_t(1) << 40)) { err = "nsteps must be positive"; return PF_EINVAL; }
     if (A->wrt <= 0 || A->wrt > 7) { err = "wrt must be a non-empty set of PF_ADJ_* bits"; return PF_EINVAL; }
+    if (A->mode != PF_ADJ_TANGENT && A->mode != PF_ADJ_REVERSE) { err = "mode must be PF_ADJ_TANGENT or PF_ADJ_REVERSE"; return PF_EINVAL; }
+    if (A->checkpoint_every < 0) { err = "checkpoint_every must be >= 0"; return PF_EINVAL; }
     const int64_t nmax = (P.precision == PF_FP64) ? 2048 : 4096;
     if (D.n_instances <= 0 || !D.n || !D.v_pull || !D.phi0 || !D.cs0 || !D.cl0) { err = "empty batch or null array"; return PF_EINVAL; }
     for (int i = 0; i < D.n_instances; ++i) {
@@ -1088,7 +1829,11 @@ int run_adjoint(const pf_adjoint_desc* A, pf_adjoint_result* R, void* stream, st
     if (e == cudaSuccess) e = cudaStreamWaitEvent(work, ev, 0);
     int rc = PF_ECUDA;
     if (e == cudaSuccess) {
-        rc = (P.precision == PF_FP64) ? run_adjoint_T<double>(*A, R, work, err) : run_adjoint_T<float>(*A, R, work, err);
+        if (A->mode == PF_ADJ_REVERSE)
+            rc = (P.precision == PF_FP64) ? run_adjoint_reverse_T<double>(*A, R, work, err)
+                                          : run_adjoint_reverse_T<float>(*A, R, work, err);
+        else
+            rc = (P.precision == PF_FP64) ? run_adjoint_T<double>(*A, R, work, err) : run_adjoint_T<float>(*A, R, work, err);
         cudaError_t e2 = cudaEventRecord(ev, work);
         if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(caller, ev, 0);
         if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(work);

@@ -71,7 +71,8 @@ class pf_batch_result(ctypes.Structure):
 
 class pf_adjoint_desc(ctypes.Structure):
     _fields_ = [("batch", pf_batch_desc), ("nsteps", ctypes.c_int64), ("wrt", ctypes.c_int),
-                ("k_target", ctypes.POINTER(ctypes.c_double))]
+                ("k_target", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int),
+                ("checkpoint_every", ctypes.c_int)]
 
 
 class pf_adjoint_result(ctypes.Structure):
@@ -80,6 +81,7 @@ class pf_adjoint_result(ctypes.Structure):
 
 
 ADJ_MPHI, ADJ_A, ADJ_B = 1, 2, 4
+ADJ_TANGENT, ADJ_REVERSE = 0, 1
 ADJ_PARAMS = ("M_phi", "A", "b")
 
 
@@ -344,9 +346,11 @@ def _batch_desc(pr, lengths, v_pull, phi0, cs0, cl0, precision, dt, keep):
 
 def adjoint(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, *, k_target=None,
             wrt=("M_phi", "A", "b"), precision="fp32", dt=None, steps_per_launch=0,
-            cells_per_thread=0, stream=None):
+            cells_per_thread=0, stream=None, mode="tangent", checkpoint_every=0):
     """pf_adjoint: k_i = c_inf / max c after `nsteps` steps of every pulled front
-    and the exact derivatives dk_i/d(M_phi, A, b) of the discrete run.
+    and the exact derivatives dk_i/d(M_phi, A, b) of the discrete run, by the
+    tangent-linear run (mode="tangent") or by a reverse sweep with stored
+    checkpoints (mode="reverse", every `checkpoint_every` steps, 0: ~sqrt(nsteps)).
 
     Same instance description as run_batch.  Returns dict(k, dk (N x 3), loss,
     grad (3,), gpu_ms); loss and grad are those of sum (k - k_target)^2.
@@ -360,6 +364,8 @@ def adjoint(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, *, k_target=None,
     A.batch = D
     A.nsteps = int(nsteps)
     A.wrt = sum(1 << ADJ_PARAMS.index(w) for w in wrt)
+    A.mode = {"tangent": ADJ_TANGENT, "reverse": ADJ_REVERSE}[mode]
+    A.checkpoint_every = int(checkpoint_every)
     kt = None
     if k_target is not None:
         kt = np.ascontiguousarray(k_target, dtype=np.float64)

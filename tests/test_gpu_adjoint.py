@@ -172,3 +172,50 @@ def test_torch_autograd_loss():
         losses.append(float(l.detach()))
     assert losses[-1] < 0.2 * losses[0], losses
 
+
+
+# ------------------------------------------------------------ reverse sweep
+
+def test_reverse_sweep_matches_tangent_fp64():
+    """PF_ADJ_REVERSE (checkpoints every 37 steps, re-run and swept backwards
+    with the adjoint of the fused step) gives the same k and dk/d(M_phi, A, b)
+    as the tangent-linear run, over segments that straddle window shifts."""
+    lengths, vs = [128, 200, 256], [0.1, 0.3, 0.6]
+    prs, dts, phi, cs, cl = inputs(lengths, vs, A=1.2, b=0.8)
+    nsteps = 400
+    rt = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, nsteps, precision="fp64", dt=dts)
+    rr = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, nsteps, precision="fp64", dt=dts, mode="reverse",
+                    checkpoint_every=37)
+    assert np.abs(rr["k"] - rt["k"]).max() <= 1e-13 * np.abs(rt["k"]).max()
+    for j, name in enumerate(PARAMS):
+        err = np.abs(rr["dk"][:, j] - rt["dk"][:, j]).max() / np.abs(rt["dk"][:, j]).max()
+        assert err <= 1e-9, (name, err, rr["dk"][:, j], rt["dk"][:, j])
+
+
+def test_reverse_sweep_matches_oracle_finite_differences():
+    lengths, vs = [128, 200], [0.1, 0.3]
+    prs, dts, phi, cs, cl = inputs(lengths, vs)
+    nsteps = 400
+    r = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, nsteps, precision="fp64", dt=dts, mode="reverse")
+    for j, name in enumerate(PARAMS):
+        fd = richardson(lambda t: k_oracle(prs, dts, lengths, phi, cs, cl, nsteps, **{name: t}), prs[0][name])
+        err = np.abs(r["dk"][:, j] - fd).max() / np.abs(fd).max()
+        assert err <= 1e-6, (name, err)
+
+
+def test_reverse_sweep_fp32_and_loss():
+    lengths, vs = [300, 500], [0.1, 0.4]
+    prs, dts, phi, cs, cl = inputs(lengths, vs)
+    kt = np.array([0.4, 0.6])
+    r64 = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 600, precision="fp64", dt=dts, k_target=kt)
+    r32 = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 600, precision="fp32", dt=dts, k_target=kt,
+                     mode="reverse")
+    assert np.abs(r32["k"] - r64["k"]).max() <= 1e-5
+    for j in range(3):
+        err = np.abs(r32["dk"][:, j] - r64["dk"][:, j]).max() / np.abs(r64["dk"][:, j]).max()
+        assert err <= 1e-3, (PARAMS[j], err)
+    res = r32["k"] - kt
+    np.testing.assert_allclose(r32["grad"], (2 * res[:, None] * r32["dk"]).sum(0), rtol=1e-12, atol=0)
+    ra = pf.adjoint(prs[0], lengths, vs, phi, cs, cl, 600, precision="fp32", dt=dts, k_target=kt,
+                    mode="reverse", wrt=("b",))
+    assert np.all(ra["dk"][:, :2] == 0)
