@@ -318,6 +318,11 @@ def run_adjoint(args):
     adj = pf.adjoint(prs[0], lengths, vs, *f32, K, k_target=kt, dt=dts, steps_per_launch=spl)
     adj_wall = time.perf_counter() - t0
     ratio = adj["gpu_ms"] / fwd["gpu_ms"]
+    # the same derivatives by the reverse sweep (checkpoints every ~sqrt(K) steps)
+    pf.adjoint(prs[0], lengths, vs, *f32, spl, k_target=kt, dt=dts, mode="reverse")             # warm-up
+    t0 = time.perf_counter()
+    rev = pf.adjoint(prs[0], lengths, vs, *f32, K, k_target=kt, dt=dts, mode="reverse")
+    rev_wall = time.perf_counter() - t0
     out = {"metric": "adjoint/forward cost ratio (d k_i / d(M_phi, A, b), 16 pulled fronts x 2048 cells)",
            "value": ratio, "unit": "ratio of device times", "n_gpus": 1, "steps": K,
            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
@@ -328,7 +333,12 @@ def run_adjoint(args):
            "adjoint_gpu_s": adj["gpu_ms"] * 1e-3, "adjoint_wall_s": adj_wall,
            "wall_ratio": adj_wall / fwd_wall,
            "k_forward_vs_adjoint_max_abs": float(np.abs(fwd["k_v"] - adj["k"]).max()),
-           "loss": adj["loss"], "grad": [float(g) for g in adj["grad"]]}
+           "loss": adj["loss"], "grad": [float(g) for g in adj["grad"]],
+           "reverse": {"gpu_s": rev["gpu_ms"] * 1e-3, "wall_s": rev_wall,
+                       "cost_ratio": rev["gpu_ms"] / fwd["gpu_ms"],
+                       "dk_vs_tangent_max_rel": float(np.abs(rev["dk"] - adj["dk"]).max()
+                                                      / np.abs(adj["dk"]).max()),
+                       "path": "reverse sweep of the fused step, checkpoints every ceil(sqrt(K)) steps"}}
     if args.calibrate > 0:
         # Adam on log(M_phi, A, b) towards the target curve, one pf_adjoint per iteration
         t0 = time.perf_counter()

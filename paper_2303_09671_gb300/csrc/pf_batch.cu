@@ -63,8 +63,8 @@ struct BatchArgs {
     int energy_slots;               // records per instance in `energy`
     double* energy;                 // [instance][slot] F_h records (device)
     double dir_phi;                 // hot-end ghost phi, for the gradient energy
-    T* rec;                         // if set: the state before every step of the launch,
-                                    // [instance block of 3 rec_steps n][step][phi|c|d][n]
+    T* rec;                         // if set: every step's state and intermediates,
+                                    // [instance block of 6 rec_steps n][step][phi|c|d|mu_s|mu_l|phidot][n]
     long long rec_steps;
 };
 
@@ -138,12 +138,13 @@ batch_kernel(BatchArgs<T> a) {
     for (int it = 0; it < a.nsteps; ++it) {
         const double t = (double)step * a.dt[inst];
         const T theta0 = T(a.theta_ref + a.G_theta * (a.x0 + v * t - (double)shifts * (double)C.dx));
-        if (a.rec != nullptr) {   // the pre-step state, for a reverse sweep
-            T* r = a.rec + 3 * a.rec_steps * off + (long long)it * 3 * n;
+        // for a reverse sweep: the pre-step state, then mu_s, mu_l, phidot below
+        T* const rec = a.rec != nullptr ? a.rec + 6 * a.rec_steps * off + (long long)it * 6 * n : nullptr;
+        if (rec != nullptr) {
             for (int i = tid; i < n; i += NT) {
-                r[i] = sPhi[i];
-                r[n + i] = sC[i];
-                r[2 * n + i] = sD[i];
+                rec[i] = sPhi[i];
+                rec[n + i] = sC[i];
+                rec[2 * n + i] = sD[i];
             }
         }
         // P1: diffusion potentials
@@ -152,6 +153,10 @@ batch_kernel(BatchArgs<T> a) {
             cs_cl(i, p, cs, cl);
             sMs[i] = flog(cs) - C.log_ke;
             sMl[i] = flog(cl);
+            if (rec != nullptr) {
+                rec[3 * n + i] = sMs[i];
+                rec[4 * n + i] = sMl[i];
+            }
         }
         __syncthreads();
         // P2: phase-field rate (cold end: mirror ghost; hot end: Dirichlet or
@@ -191,6 +196,7 @@ batch_kernel(BatchArgs<T> a) {
             const T R = C.sigma * lap - C.H * dfdw - dG * dp +
                         C.one_m_A * d * pq * iMbar * (Ms * gs - bMl * gl) * gp * rr;
             sPd[i] = R / Kc;
+            if (rec != nullptr) rec[5 * n + i] = sPd[i];
         }
         __syncthreads();
         // P3: faces of each owned cell and the new state (kept in registers)
@@ -1165,7 +1171,7 @@ __device__ void face1_rev(const Consts<T>& C, T fL, T fR, T csL, T csR, T clL, T
 
 template <typename T>
 struct RevArgs {
-    const T* rec;            // recorded pre-step states of the segment (batch_kernel layout)
+    const T* rec;            // recorded states and intermediates of the segment (batch_kernel layout)
     long long rec_steps;
     T* lphi;                 // adjoint state, packed like the value state
     T* lc;
@@ -1258,8 +1264,8 @@ __global__ void __launch_bounds__(NT, 1) reverse_kernel(RevArgs<T> a) {
             }
             __syncthreads();
         }
-        // forward values of the step from the recorded state
-        const T* r = a.rec + 3 * a.rec_steps * off + (long long)it * 3 * n;
+        // the step's state and intermediates, as the forward run recorded them
+        const T* r = a.rec + 6 * a.rec_steps * off + (long long)it * 6 * n;
         T dval[RJ], pval[RJ];
 #pragma unroll
         for (int j = 0; j < RJ; ++j) {
@@ -1267,50 +1273,17 @@ __global__ void __launch_bounds__(NT, 1) reverse_kernel(RevArgs<T> a) {
             if (i >= n) break;
             const T f = r[i], c = r[n + i], d = r[2 * n + i];
             const T p = p_of(C, f);
-            const T cs = c + (T(1) - p) * d, cl = c - p * d;
             sF[i] = f;
-            sCs[i] = cs;
-            sCl[i] = cl;
-            sMs[i] = flog(cs) - C.log_ke;
-            sMl[i] = flog(cl);
+            sCs[i] = c + (T(1) - p) * d;
+            sCl[i] = c - p * d;
+            sMs[i] = r[3 * n + i];
+            sMl[i] = r[4 * n + i];
+            sPd[i] = r[5 * n + i];
             dval[j] = d;
             pval[j] = p;
         }
         __syncthreads();
         const T theta0 = T(th0[it]);
-#pragma unroll
-        for (int j = 0; j < RJ; ++j) {   // phidot, as batch_kernel (Dirichlet hot end)
-            const int i = tid + j * NT;
-            if (i >= n) break;
-            const int im = (i == 0) ? 0 : i - 1;
-            const bool last = i == n - 1;
-            const T fc = sF[i], fW = sF[im], fE = last ? a.gphi : sF[i + 1];
-            const T mWs = sMs[im], mWl = sMl[im];
-            const T mEs = last ? a.gmus : sMs[i + 1], mEl = last ? a.gmul : sMl[i + 1];
-            const T p = pval[j], cs = sCs[i], cl = sCl[i], mus = sMs[i], mul = sMl[i];
-            const T dp = dp_of(C, fc);
-            const T lap = (fW - T(2) * fc + fE) * C.inv_dx2;
-            const T gp = (fE - fW) * C.inv_2dx;
-            const T gs = (mEs - mWs) * C.inv_2dx;
-            const T gl = (mEl - mWl) * C.inv_2dx;
-            const T Ms = Ms_of(C, cs), Ml = Ml_of(C, cl);
-            const T bMl = C.b * Ml;
-            const T Msq = Ms * (T(1) - p);
-            const T iM = T(1) / (Msq + bMl * p);
-            const T d = cs - cl;
-            const T rr = T(1) / (gp * gp + C.delta2);
-            const T pq = p * (T(1) - p);
-            const T Kc = C.inv_Mphi + C.one_m_A * C.one_m_A * d * d * C.b * pq * rr * iM / (C.b * p + T(1) - p);
-            const T theta = theta0 - C.G_theta * ((T(i) + T(0.5)) * C.dx);
-            const T dmu = mus - mul;
-            const T Dd = (Msq * (T(1) - C.A * (T(1) - p)) + C.A * bMl * p * p) * iM;
-            const T dG = cs * dmu - d - C.one_m_ke * theta - Dd * d * dmu;
-            const T dfdw = T(2) * fc * (T(1) - fc) * (T(1) - T(2) * fc);
-            const T R = C.sigma * lap - C.H * dfdw - dG * dp +
-                        C.one_m_A * d * pq * iM * (Ms * gs - bMl * gl) * gp * rr;
-            sPd[i] = R / Kc;
-        }
-        __syncthreads();
         // R1: the two faces of each cell, their parts that act on the cell
         T aF[RJ], aCs[RJ], aCl[RJ], aMs[RJ], aMl[RJ], aP[RJ], aPd[RJ];
 #pragma unroll
@@ -1636,7 +1609,7 @@ static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R,
     if (e == cudaSuccess) e = cudaMalloc(&ckc, fb * nseg);
     if (e == cudaSuccess) e = cudaMalloc(&ckd, fb * nseg);
     if (e == cudaSuccess) e = cudaMalloc(&ckst, (size_t)N * nseg * sizeof(BatchState));
-    if (e == cudaSuccess) e = cudaMalloc(&rec, fb * 3 * seg);
+    if (e == cudaSuccess) e = cudaMalloc(&rec, fb * 6 * seg * 2);
     if (e == cudaSuccess) e = cudaMalloc(&lphi, fb);
     if (e == cudaSuccess) e = cudaMalloc(&lc, fb);
     if (e == cudaSuccess) e = cudaMalloc(&ld, fb);
@@ -1718,21 +1691,43 @@ static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R,
         seed_lambda<V><<<(N + 255) / 256, 256, 0, main>>>(lc, B.st, cmax, imax, D.params.c_inf, N);
         e = cudaGetLastError();
     }
-    // backwards: re-run each segment recording every step, then sweep it
-    B.rec = rec;
+    // backwards: re-run each segment recording every step (main stream, the
+    // batch kernel) and sweep it (a second stream, the reverse kernel).  The
+    // records are double-buffered, so the re-run of segment s-1 overlaps the
+    // sweep of segment s; the sweeps run in order on their stream.
+    cudaStream_t rs = nullptr;
+    cudaEvent_t erec[2] = {nullptr, nullptr}, erev[2] = {nullptr, nullptr};
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&erec[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&erev[b], cudaEventDisableTiming);
+    }
     B.rec_steps = seg;
-    for (int64_t s = nseg - 1; s >= 0 && e == cudaSuccess; --s) {
+    const size_t rec_elems = (size_t)6 * seg * B.total;
+    auto rerun = [&](int64_t s) {
+        const int b = (int)(s & 1);
         const int64_t len = std::min(seg, A.nsteps - s * seg);
-        e = cudaMemcpyAsync(B.phi, ckp + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(B.c, ckc + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(B.d, ckd + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(B.st, ckst + s * N, N * sizeof(BatchState), cudaMemcpyDeviceToDevice, main);
-        if (e == cudaSuccess) e = B.issue((int)len);
+        cudaError_t x = cudaSuccess;
+        if (s + 2 < nseg) x = cudaStreamWaitEvent(main, erev[b], 0);   // the sweep of s+2 read this buffer
+        if (x == cudaSuccess) x = cudaMemcpyAsync(B.phi, ckp + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
+        if (x == cudaSuccess) x = cudaMemcpyAsync(B.c, ckc + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
+        if (x == cudaSuccess) x = cudaMemcpyAsync(B.d, ckd + s * B.total, fb, cudaMemcpyDeviceToDevice, main);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(B.st, ckst + s * N, N * sizeof(BatchState), cudaMemcpyDeviceToDevice, main);
+        B.rec = rec + b * rec_elems;
+        if (x == cudaSuccess) x = B.issue((int)len);
+        if (x == cudaSuccess) x = cudaEventRecord(erec[b], main);
+        return x;
+    };
+    if (e == cudaSuccess) e = rerun(nseg - 1);
+    for (int64_t s = nseg - 1; s >= 0 && e == cudaSuccess; --s) {
+        const int b = (int)(s & 1);
+        const int64_t len = std::min(seg, A.nsteps - s * seg);
+        e = cudaStreamWaitEvent(rs, erec[b], 0);
         if (e == cudaSuccess) {
             const BatchArgs<V> ba = B.args(B.groups[0], (int)len);
             RevArgs<V> ra;
-            ra.rec = rec;
+            ra.rec = rec + b * rec_elems;
             ra.rec_steps = seg;
             ra.lphi = lphi;
             ra.lc = lc;
@@ -1751,9 +1746,20 @@ static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R,
             ra.gcl = ba.gcl;
             ra.gmus = ba.gmus;
             ra.gmul = ba.gmul;
-            reverse_kernel<V, NT, RJ><<<N, NT, rsmem, main>>>(ra);
+            reverse_kernel<V, NT, RJ><<<N, NT, rsmem, rs>>>(ra);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaEventRecord(erev[b], rs);
+        if (e == cudaSuccess && s > 0) e = rerun(s - 1);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, erev[0], 0);   // the sweep of segment 0
+    if (rs) {
+        cudaStreamSynchronize(rs);
+        cudaStreamDestroy(rs);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (erec[b]) cudaEventDestroy(erec[b]);
+        if (erev[b]) cudaEventDestroy(erev[b]);
     }
     if (e == cudaSuccess) e = cudaEventRecord(B.t1, main);
     std::vector<double> hg(3 * N), hc(N);
