@@ -384,7 +384,7 @@ def adjoint(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, *, k_target=None,
 
 def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, iters=50, lr=0.05,
               wrt=("M_phi", "A", "b"), precision="fp32", dt=None, betas=(0.9, 0.999), eps=1e-8,
-              callback=None):
+              callback=None, mode="tangent"):
     """Adam on the logarithms of the chosen parameters (M_phi, A, b > 0), each
     iteration one pf_adjoint run; returns (parameters, history of losses)."""
     idx = [ADJ_PARAMS.index(w) for w in wrt]
@@ -397,7 +397,7 @@ def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, it
         for j, t in zip(idx, theta):
             cur[ADJ_PARAMS[j]] = float(np.exp(t))
         r = adjoint(cur, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target=k_target, wrt=wrt,
-                    precision=precision, dt=dt)
+                    precision=precision, dt=dt, mode=mode)
         hist.append(r["loss"])
         g = np.array([r["grad"][j] for j in idx]) * np.exp(theta)   # d/d(log theta)
         m = betas[0] * m + (1 - betas[0]) * g
@@ -414,17 +414,20 @@ def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, it
 
 class KvProblem:
     """The fixed part of a k(V) calibration problem for kv_loss: instances,
-    initial fields, step count, targets, precision."""
+    initial fields, step count, targets, precision, and how the gradient is
+    taken (mode="reverse": the reverse sweep with checkpoints; "tangent")."""
 
-    def __init__(self, pr, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, precision="fp32", dt=None):
+    def __init__(self, pr, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, precision="fp32", dt=None,
+                 mode="reverse"):
         self.pr, self.lengths, self.v_pull = dict(pr), lengths, v_pull
         self.fields = (phi0, cs0, cl0)
         self.nsteps, self.k_target, self.precision, self.dt = nsteps, k_target, precision, dt
+        self.mode = mode
 
     def run(self, theta):
         pr = dict(self.pr, **{n: float(t) for n, t in zip(ADJ_PARAMS, theta)})
         return adjoint(pr, self.lengths, self.v_pull, *self.fields, self.nsteps, k_target=self.k_target,
-                       precision=self.precision, dt=self.dt)
+                       precision=self.precision, dt=self.dt, mode=self.mode)
 
 
 def kv_loss(theta, problem: KvProblem):

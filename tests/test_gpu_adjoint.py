@@ -147,8 +147,8 @@ def test_adam_calibration_lowers_the_loss():
 
 
 def test_torch_autograd_loss():
-    """kv_loss as a torch.autograd function: its gradient is pf_adjoint's, and
-    torch's own Adam on it lowers the loss."""
+    """kv_loss as a torch.autograd function (gradient by the reverse sweep): its
+    gradient is pf_adjoint's, and torch's own Adam on it lowers the loss."""
     torch = pytest.importorskip("torch")
     lengths, vs = [160, 200], [0.1, 0.3]
     prs, dts, phi, cs, cl = inputs(lengths, vs, A=1.15)
