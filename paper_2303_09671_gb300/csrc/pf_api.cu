@@ -79,6 +79,10 @@ std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
     if (g->n[0] > (1 << 30) || g->n[1] > (1 << 30) || g->n[2] > (1 << 30) ||
         g->n[0] * g->n[1] * g->n[2] > (int64_t(1) << 34))
         return "grid too large";
+    // launch limits of the 2D/3D kernels: one CTA row per 8 or 16 cells of y in
+    // grid.y (at most 65535), and 32-bit offsets within an x-y plane
+    if (g->dim >= 2 && g->n[1] > int64_t(65535) * 8) return "n[1] above 524280 is not supported";
+    if (g->dim == 3 && g->n[0] * g->n[1] > int64_t(0x7fffffff)) return "an x-y plane above 2^31 - 1 cells is not supported";
     if (!(g->dx > 0)) return "dx must be positive";
     if (p->precision != PF_FP32 && p->precision != PF_FP64) return "precision must be PF_FP32 or PF_FP64";
     if (p->interp != PF_INTERP_QUINTIC && p->interp != PF_INTERP_CUBIC) return "unknown interp";

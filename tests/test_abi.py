@@ -85,3 +85,19 @@ def test_null_handle_calls_fail_cleanly():
 def test_stable_dt_matches_recipe(maker):
     pr = maker()[0]
     assert abs(pf.stable_dt(pr) - wl.stable_dt(pr)) <= 1e-13 * wl.stable_dt(pr)
+
+
+def test_create_rejects_grids_beyond_the_launch_limits():
+    """y extents the 2D/3D kernels cannot tile (grid.y <= 65535) and x-y planes
+    beyond 32-bit offsets are refused before any allocation."""
+    pr, *_ = wl.random_state(2, (16, 8))
+    g, b, p = pf.make_structs(pr, "fp32")
+    g.n[1] = 65535 * 8 + 1
+    h = ctypes.c_void_p()
+    rc = pf.lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == pf.PF_EINVAL and "n[1]" in pf.lib().pf_last_error(None).decode()
+    pr, *_ = wl.random_state(3, (16, 8, 8))
+    g, b, p = pf.make_structs(pr, "fp32")
+    g.n[0], g.n[1], g.n[2] = 1 << 17, 1 << 14, 3
+    rc = pf.lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == pf.PF_EINVAL and "plane" in pf.lib().pf_last_error(None).decode()

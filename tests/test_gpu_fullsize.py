@@ -70,3 +70,37 @@ def test_perturbed_front_1024_squared(precision):
     assert tuple(pr["n"]) == (1024, 1024) and pr["lap"] == 9
     st, g = advance(pr, (phi, cs, cl), 50, precision)
     check(pr, st, g, precision)
+
+
+def test_beyond_2_31_cells_planar_3d():
+    """A 3D FP32 grid of 2048 x 1024 x 1040 = 2.18e9 cells (more than 2^31) with a
+    planar front along x, set and read through device pointers: after three
+    steps every (y, z) column is the same, bit for bit (64-bit cell indexing
+    everywhere), and a column follows the FP64 oracle's 1D run to 1e-5."""
+    torch = pytest.importorskip("torch")
+    nx, ny, nz = 2048, 1024, 1040
+    cells = nx * ny * nz
+    assert cells > 2 ** 31
+    # the handle's 8 state arrays and the 6 field tensors, 4 B each
+    if torch.cuda.mem_get_info()[0] < 1.1 * 14 * 4 * cells:
+        pytest.skip("not enough device memory for a grid beyond 2^31 cells")
+    pr1, phi1, cs1, cl1 = wl.planar_1d(N=nx, dx=0.5, front_cell=nx // 2, A=1.0, b=1.0)
+    pr3 = dict(pr1, dim=3, n=(nx, ny, nz), lap=19, bc_lo=("noflux", "periodic", "periodic"),
+               bc_hi=("noflux", "periodic", "periodic"))
+    pr3["dt"] = 0.9 * wl.stable_dt(pr3)
+    pr1 = dict(pr1, dt=pr3["dt"])
+    f1 = [np.asarray(a, np.float32) for a in (phi1, cs1, cl1)]
+    st = oracle.State(pr1, *(a.astype(np.float64) for a in f1))
+    st.step(3)
+    dev = [torch.from_numpy(a).cuda().reshape(1, 1, nx).expand(nz, ny, nx).contiguous() for a in f1]
+    with Sim(pr3, "fp32") as s:
+        s.set_fields(*dev)
+        del dev
+        s.step(3)
+        out = [torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda") for _ in range(3)]
+        s.get_fields(out=out)
+    for a in out:
+        col = a[:1, :1, :]
+        assert bool(torch.eq(a, col).all()), "columns differ"
+    got = out[0][0, 0].double().cpu().numpy()
+    assert np.abs(got - st.phi).max() <= 1e-5, np.abs(got - st.phi).max()
