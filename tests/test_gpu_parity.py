@@ -159,6 +159,31 @@ def test_fp64_generic_cross_check_kernel(dim, monkeypatch):
     assert_fields(st, g, TOL64, pr)
 
 
+@pytest.mark.parametrize("dim,n", [(1, (90,)), (2, (45, 19)), (3, (37, 19, 13))])
+@pytest.mark.parametrize("opts", [dict(interp="cubic"), dict(mobility="const"),
+                                  dict(interp="cubic", mobility="const", a=-0.3)])
+def test_fp64_interpolation_and_mobility_options(dim, n, opts):
+    """The cubic h(phi) and the constant mobilities M_i = D_i, alone and together,
+    through every kernel (1D generic, 2D and 3D paired)."""
+    kw = dict(dict(A=1.5, b=0.3, a=0.0), **opts)
+    pr, phi, cs, cl = wl.random_state(dim, n, dx=0.5, seed=14, **kw)
+    st, g, _ = run_pair(pr, phi, cs, cl, 30)
+    assert_fields(st, g, TOL64, pr)
+
+
+@pytest.mark.parametrize("dim,n", [(2, (45, 19)), (3, (37, 19, 13))])
+@pytest.mark.parametrize("phase", [0.0, 1.0])
+def test_fp64_single_phase(dim, n, phase):
+    """Degenerate states: all liquid (phi = 0) or all solid (phi = 1), p' = 0
+    and grad phi = 0 everywhere, so phi stays put and only the concentrations
+    diffuse (no 0/0 anywhere)."""
+    pr, _, cs, cl = wl.random_state(dim, n, dx=0.5, A=1.5, b=0.3, seed=15)
+    phi = np.full_like(cs, phase)
+    st, g, _ = run_pair(pr, phi, cs, cl, 30)
+    assert np.all(g[0] == phase)
+    assert_fields(st, g, TOL64, pr)
+
+
 def test_fp64_1d_pulled_front_shift():
     pr, phi, cs, cl = wl.pulled_front_1d(N=512, V=0.2, A=1.0, b=1.0)
     st, g, clock = run_pair(pr, phi, cs, cl, 600)
