@@ -1554,20 +1554,20 @@ __global__ void seed_lambda(V* __restrict__ lc, const BatchState* __restrict__ s
     if (i < N && imax[i] >= 0 && imax[i] < st[i].n) lc[st[i].off + imax[i]] = V(-cinf / (cmax[i] * cmax[i]));
 }
 
+// 512 threads per instance, RJ cells each: the smallest RJ that covers the
+// longest instance (registers hold RJ cells' partial adjoints)
 template <typename V>
-struct RevKernel;
-template <>
-struct RevKernel<double> {
-    static constexpr int NT = 512, RJ = 4;   // up to 2048 cells
-};
-template <>
-struct RevKernel<float> {
-    static constexpr int NT = 512, RJ = 8;   // up to 4096 cells
-};
+using RevFn = void (*)(RevArgs<V>);
+template <typename V>
+static RevFn<V> reverse_for(int64_t nmax) {
+    if (nmax <= 1024) return reverse_kernel<V, 512, 2>;
+    if (nmax <= 2048) return reverse_kernel<V, 512, 4>;
+    return reverse_kernel<V, 512, 8>;
+}
 
 template <typename V>
 static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R, cudaStream_t main, std::string& err) {
-    constexpr int NT = RevKernel<V>::NT, RJ = RevKernel<V>::RJ;
+    constexpr int NT = 512;
     pf_batch_desc D = A.batch;
     D.check_every = 0;   // a fixed number of steps
     D.energy_every = 0;
@@ -1651,9 +1651,10 @@ static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R,
             if (!setup.done[dev]) {
                 int optin = 0;
                 setup.err[dev] = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-                if (setup.err[dev] == cudaSuccess) setup.err[dev] = raise_smem(reverse_kernel<V, NT, RJ>, optin);
+                for (int64_t m : {int64_t(1024), int64_t(2048), int64_t(4096)})
+                    if (setup.err[dev] == cudaSuccess) setup.err[dev] = raise_smem(reverse_for<V>(m), optin);
                 cudaFuncAttributes fa;
-                if (setup.err[dev] == cudaSuccess) setup.err[dev] = cudaFuncGetAttributes(&fa, reverse_kernel<V, NT, RJ>);
+                if (setup.err[dev] == cudaSuccess) setup.err[dev] = cudaFuncGetAttributes(&fa, reverse_for<V>(4096));
                 setup.value[dev] = setup.err[dev] == cudaSuccess ? (size_t)optin - fa.sharedSizeBytes : 0;
                 setup.done[dev] = true;
             }
@@ -1746,7 +1747,7 @@ static int run_adjoint_reverse_T(const pf_adjoint_desc& A, pf_adjoint_result* R,
             ra.gcl = ba.gcl;
             ra.gmus = ba.gmus;
             ra.gmul = ba.gmul;
-            reverse_kernel<V, NT, RJ><<<N, NT, rsmem, rs>>>(ra);
+            reverse_for<V>(nmax)<<<N, NT, rsmem, rs>>>(ra);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(erev[b], rs);
