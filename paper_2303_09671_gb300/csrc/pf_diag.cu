@@ -2,9 +2,10 @@
 // c_max), the 1D moving-window shift and the conversions between the
 // caller's (phi, c_s, c_l) and the device state (phi, c, d[, c_lo]).
 //
-// Reductions are deterministic: a fixed grid of DIAG_BLOCKS blocks writes one
-// partial per block (warp-shuffle tree inside the block), and a single block
-// sums the partials in a fixed order.
+// Reductions are deterministic: a grid fixed by the problem size (at most
+// DIAG_BLOCKS blocks, fewer for small grids, so that a 1D run does not launch
+// a thousand idle blocks every step) writes one partial per block (warp-shuffle
+// tree inside the block), and a single block sums the partials in a fixed order.
 #include <cmath>
 #include <cstdint>
 #include "pf_internal.cuh"
@@ -16,6 +17,12 @@ static constexpr int DIAG_THREADS = 256;
 static constexpr int DIAG_BLOCKS = 1216;   // 8 per SM on a 152-SM GB300
 
 size_t diag_scratch_doubles(const HostProblem&) { return 2 * (size_t)DIAG_BLOCKS; }
+
+// blocks for a grid-stride pass over `items`
+static int diag_blocks(long long items) {
+    const long long b = (items + DIAG_THREADS - 1) / DIAG_THREADS;
+    return (int)(b < 1 ? 1 : (b > DIAG_BLOCKS ? DIAG_BLOCKS : b));
+}
 
 struct DiagConsts {
     int n[3], bc_lo[3], bc_hi[3], dim, lap, interp;
@@ -336,26 +343,28 @@ cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t 
                                  int64_t shifts, bool with_energy, double* scratch, double* out,
                                  cudaStream_t s) {
     const DiagConsts C = make_diag(P, step, shifts);
+    const int nb = diag_blocks(P.cells());
     if (P.precision == 1) {
-        if (with_energy) energy_solute_kernel<double, true><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
-        else energy_solute_kernel<double, false><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+        if (with_energy) energy_solute_kernel<double, true><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+        else energy_solute_kernel<double, false><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
     } else {
-        if (with_energy) energy_solute_kernel<float, true><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
-        else solute_f32_kernel<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+        if (with_energy) energy_solute_kernel<float, true><<<nb, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
+        else solute_f32_kernel<<<nb, DIAG_THREADS, 0, s>>>(
             (const float*)f.c, (const float*)f.clo, P.cells(), scratch);
     }
-    finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, C.dV, out);
+    finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, nb, C.dV, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_front(const HostProblem& P, const Fields& f, double* scratch, double* out,
                          cudaStream_t s) {
     const DiagConsts C = make_diag(P, 0, 0);
+    const int nb = diag_blocks(P.cells() / P.n[0]);   // one thread per x row
     if (P.precision == 1)
-        front_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+        front_kernel<double><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
     else
-        front_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
-    finish_max2<<<1, DIAG_THREADS, 0, s>>>(scratch, DIAG_BLOCKS, out);
+        front_kernel<float><<<nb, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
+    finish_max2<<<1, DIAG_THREADS, 0, s>>>(scratch, nb, out);
     return cudaGetLastError();
 }
 
