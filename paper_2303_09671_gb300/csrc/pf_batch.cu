@@ -739,8 +739,17 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
     float total_ms = 0;
     int64_t done_steps = 0;
     for (;;) {
+        // whole graph replays, then the remainder of max_steps launched directly,
+        // so that no instance takes more than max_steps steps
+        const int64_t left = D.max_steps - done_steps;
+        const bool whole = left >= per_replay;
         e = cudaEventRecord(B.t0, main);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, main);
+        if (whole) {
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, main);
+        } else {
+            for (int64_t r = left; r > 0 && e == cudaSuccess; r -= D.steps_per_launch)
+                e = B.issue((int)std::min<int64_t>(r, D.steps_per_launch));
+        }
         if (e == cudaSuccess) e = cudaEventRecord(B.t1, main);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), B.st, N * sizeof(BatchState), cudaMemcpyDeviceToHost, main);
         if (e == cudaSuccess) e = cudaStreamSynchronize(main);
@@ -748,8 +757,8 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
         float ms = 0;
         cudaEventElapsedTime(&ms, B.t0, B.t1);
         total_ms += ms;
-        B.launches += (int64_t)D.launches_per_graph * (int64_t)B.groups.size();
-        done_steps += per_replay;
+        if (whole) B.launches += (int64_t)D.launches_per_graph * (int64_t)B.groups.size();
+        done_steps += whole ? per_replay : left;
         bool all = true;
         for (int i = 0; i < N; ++i)
             if (!hs[i].converged) all = false;

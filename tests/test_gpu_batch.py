@@ -116,3 +116,20 @@ def test_closed_box_planar_front_with_energy_records():
     assert np.all(np.isfinite(E))
     assert np.abs(E - hist[1:steps + 1]).max() <= 1e-12 * np.abs(hist).max()
     assert np.all(np.diff(E) <= 1e-13 * abs(E[0]))
+
+
+def test_batch_stops_exactly_at_max_steps():
+    """A step cap that is not a multiple of the graph replay (4 launches of 100
+    steps): three replays and a directly launched remainder of 34 steps, and the
+    fields equal those of one 1234-step launch bit for bit."""
+    lengths, vs = [96, 300], [0.1, 0.2]
+    prs, phi, cs, cl = batch_inputs(lengths, vs)
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    common = dict(precision="fp64", dt=dts, check_every=50, tol=-1.0, want_fields=True, cells_per_thread=2)
+    a = pf.run_batch(prs[0], lengths, vs, phi, cs, cl, max_steps=1234, steps_per_launch=100,
+                     launches_per_graph=4, **common)
+    b = pf.run_batch(prs[0], lengths, vs, phi, cs, cl, max_steps=1234, steps_per_launch=1234,
+                     launches_per_graph=1, **common)
+    assert (a["steps"] == 1234).all() and (b["steps"] == 1234).all()
+    for k in ("phi", "cs", "cl"):
+        assert np.array_equal(a[k], b[k]), k

@@ -27,3 +27,20 @@ def test_non_finite_state_is_reported_and_recoverable(precision):
         s.set_fields(phi, cs, cl)
         s.step(3)
         assert np.isfinite(s.energy()) and np.isfinite(s.solute_total())
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    """A grid whose state does not fit in device memory (2^34 cells in FP64,
+    eight arrays of 137 GB) fails in pf_create with PF_ENOMEM, frees what it
+    had allocated, and the next handle works.  The failing call is the real
+    cudaMalloc; nothing is launched."""
+    from paper_2303_09671_gb300 import pf
+    pr, phi, cs, cl = wl.random_state(3, (16, 8, 8), dx=0.5, A=1.5, b=0.3, seed=4)
+    big = dict(pr, n=(1024, 1024, 16384))
+    with pytest.raises(PFError) as e:
+        Sim(big, "fp64")
+    assert e.value.code == pf.PF_ENOMEM
+    with Sim(pr, "fp64") as s:
+        s.set_fields(phi, cs, cl)
+        s.step(2)
+        assert np.isfinite(s.energy())

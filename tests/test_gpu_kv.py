@@ -13,9 +13,13 @@ pytestmark = pytest.mark.gpu
 def test_partition_coefficient_falls_towards_k_e_at_low_velocity():
     """k_e = 0.1, D_s/D_l = 0.1, A = b = 1, a steep frozen gradient (0.2 per W,
     so the start's undercooling is used up within ~45 W and the front settles
-    inside a 1024 W window).  Measured: k = 0.58, 0.27, 0.17, 0.15 at
-    V = 0.5, 0.2, 0.1, 0.05.  Smaller V need t ~ D_l / (k V^2) > 10^5 to settle
-    and are not used."""
+    inside a 1024 W window), run 6x10^5 steps, well past the transient
+    t ~ D_l / (k V^2) of the slowest front.  Steady state is checked by mass
+    balance (Eq. model5 in the frame of the window): the solid the front leaves
+    behind carries the alloy composition c_inf.  Measured: k = 0.130, 0.167,
+    0.266, 0.584 at V = 0.05, 0.1, 0.2, 0.5, and the solid 10-20 W behind the
+    front at c_inf to 1e-4.  (A test on |dk/dt| < 1e-6 over 50 time units stops
+    the V = 0.05 front at k = 0.150 with the solid still at 0.86 c_inf.)"""
     k_e, vs, n = 0.1, np.array([0.05, 0.1, 0.2, 0.5]), 2048
     prs, phis, css, cls = [], [], [], []
     for v in vs:
@@ -27,14 +31,18 @@ def test_partition_coefficient_falls_towards_k_e_at_low_velocity():
         cls.append(cl)
     dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
     res = pf.run_batch(prs[0], [n] * len(vs), vs, np.concatenate(phis), np.concatenate(css),
-                       np.concatenate(cls), precision="fp32", dt=dts, max_steps=200000, steps_per_launch=2000,
-                       launches_per_graph=4, check_every=200, window=50.0, tol=1e-6, min_travel=100.0,
-                       want_fields=True)
+                       np.concatenate(cls), precision="fp32", dt=dts, max_steps=600000, steps_per_launch=5000,
+                       launches_per_graph=4, check_every=5000, tol=-1.0, want_fields=True)
     k = res["k_v"]
-    assert res["converged"].all()
+    assert (res["steps"] == 600000).all()
     assert np.all(np.diff(k) > 0), k              # more trapping at higher V
-    assert k_e < k[0] < 0.2 and k[-1] > 0.5, k
+    assert k_e < k[0] < 0.14 and k[-1] > 0.5, k
+    cinf = prs[0]["c_inf"]
     for i in range(len(vs)):                       # the front settled inside the window
         f = res["phi"][i * n:(i + 1) * n]
         j = np.where((f[:-1] >= 0.5) & (f[1:] < 0.5))[0]
         assert len(j) == 1 and 64 < j[0] < n // 2
+        p = f ** 3 * (6 * f * f - 15 * f + 10)
+        c = p * res["cs"][i * n:(i + 1) * n] + (1 - p) * res["cl"][i * n:(i + 1) * n]
+        behind = c[j[0] - 40:j[0] - 20]
+        assert np.abs(behind - cinf).max() <= 1e-3 * cinf, (vs[i], behind)
