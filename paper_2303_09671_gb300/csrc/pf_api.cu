@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 #include "pf.h"
 #include "pf_kernels.h"
 
@@ -19,6 +20,8 @@ struct pf_handle {
     double* scratch = nullptr;   // diagnostics partials
     double* dres = nullptr;      // device results (4 doubles)
     double* hres = nullptr;      // pinned host results (4 doubles)
+    double* drec = nullptr;      // per-step (F_h, S_h) records of pf_step_energies
+    int64_t rec_cap = 0;
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
     bool generic = false;        // run 2D / 3D through the generic kernel (cross-check)
     bool have_front = false;
@@ -201,6 +204,7 @@ void pf_destroy(pf_handle* h) {
     if (h->scratch) cudaFree(h->scratch);
     if (h->dres) cudaFree(h->dres);
     if (h->hres) cudaFreeHost(h->hres);
+    if (h->drec) cudaFree(h->drec);
     delete h;
 }
 
@@ -331,6 +335,47 @@ int pf_energy(pf_handle* h, double* F) {
     if (rc) return rc;
     *F = h->hres[0];
     if (!std::isfinite(*F)) return fail(h, PF_ENONFINITE, "non-finite free energy");
+    return PF_OK;
+}
+
+int pf_step_energies(pf_handle* h, int64_t n, double* F) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (n < 0) return fail(h, PF_EINVAL, "negative step count");
+    if (n > 0 && !F) return fail(h, PF_EINVAL, "null output");
+    if (n == 0) return PF_OK;
+    if (h->rec_cap < n) {
+        if (h->drec) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->drec);
+            h->drec = nullptr;
+            h->rec_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->drec, 2 * (size_t)n * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->drec = nullptr;
+            return fail(h, PF_ENOMEM, std::string("record allocation failed: ") + cudaGetErrorString(e));
+        }
+        h->rec_cap = n;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        int rc = pf_step(h, 1);
+        if (rc) return rc;
+        cudaError_t e = pf::launch_energy_solute(h->P, h->buf[h->cur], h->step, h->shifts, true, h->scratch,
+                                                 h->drec + 2 * s, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "energy kernel launch");
+    }
+    std::vector<double> rec(2 * (size_t)n);
+    cudaError_t e = cudaMemcpyAsync(rec.data(), h->drec, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "record copy");
+    bool finite = true;
+    for (int64_t s = 0; s < n; ++s) {
+        F[s] = rec[2 * s];
+        finite = finite && std::isfinite(F[s]);
+    }
+    if (!finite) return fail(h, PF_ENONFINITE, "non-finite free energy");
     return PF_OK;
 }
 

@@ -18,9 +18,10 @@ static constexpr int DIAG_BLOCKS = 1216;   // 8 per SM on a 152-SM GB300
 
 size_t diag_scratch_doubles(const HostProblem&) { return 2 * (size_t)DIAG_BLOCKS; }
 
-// blocks for a grid-stride pass over `items`
+// blocks for a grid-stride pass over `items`: one per 64 items up to DIAG_BLOCKS,
+// so that small FP64 problems spread their (slow) FP64 work over many SMs
 static int diag_blocks(long long items) {
-    const long long b = (items + DIAG_THREADS - 1) / DIAG_THREADS;
+    const long long b = (items + 63) / 64;
     return (int)(b < 1 ? 1 : (b > DIAG_BLOCKS ? DIAG_BLOCKS : b));
 }
 

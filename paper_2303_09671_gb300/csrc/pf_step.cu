@@ -529,7 +529,9 @@ static cudaError_t launch_T(const StepLaunch& a) {
     const HostProblem& P = *a.prob;
     const Consts<T> C = make_consts<T>(P);
     const Clock<T> K = make_clock<T>(P, a.step, a.shifts);
-    if (P.dim == 1) return launch_tile<T, 1, 128, 1>(a, C, K);
+    // 1D: 32-cell tiles, so that a short line still spreads over many SMs
+    // (a 1024-cell FP64 line is bound by the FP64 units of the SMs it runs on)
+    if (P.dim == 1) return launch_tile<T, 1, 32, 1>(a, C, K);
     if (P.dim == 2) return a.use_generic ? launch_tile<T, 2, 32, 8>(a, C, K) : launch_step2d<T>(a, C, K);
     if (a.use_generic) return launch_tile<T, 3, 32, 8>(a, C, K);
     return launch_step3d<T>(a, C, K);
@@ -542,11 +544,11 @@ cudaError_t launch_step(const StepLaunch& a) {
 
 size_t step_smem_bytes(int precision, int dim) {
     if (precision == 1) {
-        if (dim == 1) return Tile<double, 1, 128, 1>::BYTES;
+        if (dim == 1) return Tile<double, 1, 32, 1>::BYTES;
         if (dim == 2) return Tile<double, 2, 32, 8>::BYTES;
         return Tile<double, 3, 32, 8>::BYTES;
     }
-    if (dim == 1) return Tile<float, 1, 128, 1>::BYTES;
+    if (dim == 1) return Tile<float, 1, 32, 1>::BYTES;
     if (dim == 2) return Tile<float, 2, 32, 8>::BYTES;
     return Tile<float, 3, 32, 8>::BYTES;
 }

@@ -94,6 +94,7 @@ _SIGS = {
     "pf_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "pf_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "pf_energy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "pf_step_energies": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "pf_solute_total": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pf_front": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_double)] * 3),
     "pf_get_clock": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -226,6 +227,13 @@ class Sim:
         v = ctypes.c_double()
         _check(lib().pf_energy(self._h, ctypes.byref(v)), self._h)
         return v.value
+
+    def step_energies(self, n: int) -> np.ndarray:
+        """n steps with F_h recorded on the device after each; returns the n energies."""
+        out = np.empty(int(n), dtype=np.float64)
+        _check(lib().pf_step_energies(self._h, int(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               self._h)
+        return out
 
     def solute_total(self) -> float:
         v = ctypes.c_double()

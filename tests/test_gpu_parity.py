@@ -341,3 +341,21 @@ def test_set_fields_from_pinned_host_memory(precision):
             out.append((g0, s.get_fields()))
     for a, b in zip(out[0][0] + out[0][1], out[1][0] + out[1][1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_energies_match_per_call_energies(precision):
+    """pf_step_energies records the same F_h after every step as pf_step(1) +
+    pf_energy, and leaves the same state."""
+    pr, phi, cs, cl = wl.planar_1d(N=256, front_cell=64, A=2.0, b=1.0)
+    with Sim(pr, precision) as a, Sim(pr, precision) as b:
+        a.set_fields(phi, cs, cl)
+        b.set_fields(phi, cs, cl)
+        Fa = a.step_energies(200)
+        Fb = []
+        for _ in range(200):
+            b.step(1)
+            Fb.append(b.energy())
+        assert np.array_equal(Fa, np.array(Fb))
+        assert all(np.array_equal(x, y) for x, y in zip(a.get_fields(), b.get_fields()))
+        assert np.all(np.diff(Fa) <= 1e-12 * abs(Fa[0]))
