@@ -152,9 +152,11 @@ int pf_energy(pf_handle* h, double* F);
  * F[0..n-1] (caller-owned host memory).  The energies are reduced on the device
  * after each step and copied back once at the end, so the host does not wait
  * on every step (the planar-front run of Sec. "Numerical technique", which
- * checks the energy decrease of Eq. model1.1 step by step).  Synchronises the
- * stream once; PF_ENONFINITE if any record is not finite (the steps are
- * taken). */
+ * checks the energy decrease of Eq. model1.1 step by step).  Without a moving
+ * temperature or window the steps are replayed as captured 64-step CUDA
+ * graphs on an internal stream ordered after and before the handle's.
+ * Synchronises the stream once; PF_ENONFINITE if any record is not finite
+ * (the steps are taken). */
 int pf_step_energies(pf_handle* h, int64_t n, double* F);
 
 /* Total solute S_h = dV sum_i [p_i c_s,i + (1-p_i) c_l,i] (Eq. model1), FP64.

@@ -350,7 +350,8 @@ int pf_step_energies(pf_handle* h, int64_t n, double* F) {
             h->drec = nullptr;
             h->rec_cap = 0;
         }
-        cudaError_t e = cudaMalloc(&h->drec, 2 * (size_t)n * sizeof(double));
+        // 2 n doubles of records, then the record counter
+        cudaError_t e = cudaMalloc(&h->drec, 2 * (size_t)n * sizeof(double) + sizeof(long long));
         if (e != cudaSuccess) {
             cudaGetLastError();
             h->drec = nullptr;
@@ -358,16 +359,70 @@ int pf_step_energies(pf_handle* h, int64_t n, double* F) {
         }
         h->rec_cap = n;
     }
-    for (int64_t s = 0; s < n; ++s) {
+    long long* slot = reinterpret_cast<long long*>(h->drec + 2 * h->rec_cap);
+    cudaError_t e = cudaMemsetAsync(slot, 0, sizeof(long long), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "record counter");
+    auto one = [&]() -> int {
         int rc = pf_step(h, 1);
         if (rc) return rc;
-        cudaError_t e = pf::launch_energy_solute(h->P, h->buf[h->cur], h->step, h->shifts, true, h->scratch,
-                                                 h->drec + 2 * s, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "energy kernel launch");
+        cudaError_t x = pf::launch_energy_solute(h->P, h->buf[h->cur], h->step, h->shifts, true, h->scratch,
+                                                 h->drec, h->stream, slot);
+        return x == cudaSuccess ? PF_OK : cuda_fail(h, x, "energy kernel launch");
+    };
+    int64_t done = 0;
+    // Without a moving temperature or window every step launches the same
+    // kernels with the same arguments (the ping-pong parity returns after an
+    // even count, the record slot advances on the device), so a captured block
+    // of GS steps is replayed instead of launching three kernels per step.
+    const pf::HostProblem& P = h->P;
+    constexpr int64_t GS = 64;
+    if (P.G_theta == 0.0 && P.v_pull == 0.0 && !P.shift && n >= 2 + 2 * GS) {
+        for (; done < 2; ++done)   // first uses set kernel attributes outside the capture
+            if (int rc = one()) return rc;
+        // capture and replay on a stream of our own, ordered after and before
+        // the handle's stream (which may be the legacy default stream, where
+        // capture is not allowed)
+        cudaStream_t cap = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev, 0);
+        const cudaStream_t own = h->stream;
+        const int64_t step0 = h->step;
+        const int cur0 = h->cur;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int rc = PF_OK;
+        if (e == cudaSuccess) {
+            h->stream = cap;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            for (int64_t s = 0; s < GS && e == cudaSuccess && rc == PF_OK; ++s) rc = one();
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess && rc == PF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+            h->step = step0;   // the capture advanced the host clock without running anything
+            h->cur = cur0;
+            for (; e == cudaSuccess && rc == PF_OK && n - done >= GS; done += GS) {
+                e = cudaGraphLaunch(exec, cap);
+                h->step += GS;
+            }
+            h->stream = own;
+            cudaError_t e3 = cudaEventRecord(ev, cap);
+            if (e3 == cudaSuccess) e3 = cudaStreamWaitEvent(own, ev, 0);
+            if (e == cudaSuccess) e = e3;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        if (ev) cudaEventDestroy(ev);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
     }
+    for (; done < n; ++done)
+        if (int rc = one()) return rc;
     std::vector<double> rec(2 * (size_t)n);
-    cudaError_t e = cudaMemcpyAsync(rec.data(), h->drec, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
-                                    h->stream);
+    e = cudaMemcpyAsync(rec.data(), h->drec, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "record copy");
     bool finite = true;

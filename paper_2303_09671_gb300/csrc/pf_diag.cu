@@ -130,8 +130,11 @@ energy_solute_kernel(StateView<T> S, DiagConsts C, double* __restrict__ part) {
     }
 }
 
+// out[0..1] = the two sums; with `slot`, out[2 k..2 k+1] for k = *slot, then
+// *slot = k + 1 (a record written from a replayed graph)
 __global__ void __launch_bounds__(DIAG_THREADS)
-finish_sum2(const double* __restrict__ part, int nb, double scale, double* __restrict__ out) {
+finish_sum2(const double* __restrict__ part, int nb, double scale, double* __restrict__ out,
+            long long* __restrict__ slot) {
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         a += part[i];
@@ -139,8 +142,13 @@ finish_sum2(const double* __restrict__ part, int nb, double scale, double* __res
     }
     block_reduce2<false>(a, b);
     if (threadIdx.x == 0) {
-        out[0] = a * scale;
-        out[1] = b * scale;
+        long long k = 0;
+        if (slot != nullptr) {
+            k = *slot;
+            *slot = k + 1;
+        }
+        out[2 * k] = a * scale;
+        out[2 * k + 1] = b * scale;
     }
 }
 
@@ -342,7 +350,7 @@ static StateView<T> view(const Fields& f) {
 
 cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t step,
                                  int64_t shifts, bool with_energy, double* scratch, double* out,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, long long* slot) {
     const DiagConsts C = make_diag(P, step, shifts);
     const int nb = diag_blocks(P.cells());
     if (P.precision == 1) {
@@ -353,7 +361,7 @@ cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t 
         else solute_f32_kernel<<<nb, DIAG_THREADS, 0, s>>>(
             (const float*)f.c, (const float*)f.clo, P.cells(), scratch);
     }
-    finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, nb, C.dV, out);
+    finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, nb, C.dV, out, slot);
     return cudaGetLastError();
 }
 

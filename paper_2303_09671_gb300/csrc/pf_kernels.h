@@ -55,7 +55,7 @@ size_t step_smem_bytes(int precision, int dim);
 size_t diag_scratch_doubles(const HostProblem& P);
 cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t step,
                                  int64_t shifts, bool with_energy, double* scratch, double* out,
-                                 cudaStream_t s);
+                                 cudaStream_t s, long long* slot = nullptr);
 cudaError_t launch_front(const HostProblem& P, const Fields& f, double* scratch, double* out,
                          cudaStream_t s);
 // moving window: out[i] = in[i+1] (i < n-1), out[n-1] = the Dirichlet state (1D)
