@@ -344,10 +344,18 @@ def test_set_fields_from_pinned_host_memory(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_step_energies_match_per_call_energies(precision):
+@pytest.mark.parametrize("case", ["planar1d", "pulled1d", "random3d"])
+def test_step_energies_match_per_call_energies(precision, case):
     """pf_step_energies records the same F_h after every step as pf_step(1) +
-    pf_energy, and leaves the same state."""
-    pr, phi, cs, cl = wl.planar_1d(N=256, front_cell=64, A=2.0, b=1.0)
+    pf_energy, and leaves the same state: through replayed graphs (isothermal
+    1D and 3D) and through direct launches (a pulled front with a moving
+    window and temperature)."""
+    if case == "planar1d":
+        pr, phi, cs, cl = wl.planar_1d(N=256, front_cell=64, A=2.0, b=1.0)
+    elif case == "pulled1d":
+        pr, phi, cs, cl = wl.pulled_front_1d(N=256, V=0.2, A=1.0, b=1.0)
+    else:
+        pr, phi, cs, cl = wl.random_state(3, (37, 19, 13), dx=0.5, A=1.5, b=0.3, a=-0.3, seed=16)
     with Sim(pr, precision) as a, Sim(pr, precision) as b:
         a.set_fields(phi, cs, cl)
         b.set_fields(phi, cs, cl)
@@ -358,4 +366,6 @@ def test_step_energies_match_per_call_energies(precision):
             Fb.append(b.energy())
         assert np.array_equal(Fa, np.array(Fb))
         assert all(np.array_equal(x, y) for x, y in zip(a.get_fields(), b.get_fields()))
-        assert np.all(np.diff(Fa) <= 1e-12 * abs(Fa[0]))
+        assert a.clock == b.clock
+        if case == "planar1d":
+            assert np.all(np.diff(Fa) <= 1e-12 * abs(Fa[0]))
