@@ -124,7 +124,9 @@ typedef struct pf_handle pf_handle;
  * environment variables, read here, select kernels for testing and tuning:
  * PF_GENERIC=1 runs 2D and 3D through the one-cell-per-thread kernel instead
  * of the paired two-lane kernels (a cross-check; same results to rounding),
- * PF_ZCHUNK=<planes> fixes the z-chunk of the 3D kernel. */
+ * PF_ZCHUNK=<planes> fixes the z-chunk of the 3D kernel,
+ * PF_OVCHUNK=<planes> the slab length of pf_set_fields_step (default 16, at most
+ * the z-chunk when that is fixed). */
 int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
               void* stream, pf_handle** out);
 
@@ -140,6 +142,24 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
 
 /* Advance n >= 0 forward-Euler steps (stream-ordered, no host sync). */
 int pf_step(pf_handle* h, int64_t n);
+
+/* pf_set_fields(h, phi, cs, cl, where) followed by pf_step(h, n), with the same
+ * results bit for bit, for a state that arrives from the host before a run
+ * (the forward-Euler step of Sec. "Numerical technique" applied to fields
+ * read from page-locked host memory).  On a 3D grid of the paired kernel with
+ * device memory or page-locked host memory and n >= 1, the fields are
+ * converted slab by slab (16 planes each by default; the first step runs with
+ * z-chunks of the same length, results being independent of it) on an internal
+ * stream, and the first step of each chunk starts, on further internal
+ * streams, as soon as the planes it reads (two below, one above the chunk,
+ * wrapped on a periodic z axis) are in, so that stepping overlaps the
+ * transfer.  The handle's stream waits for all of it; the remaining n - 1
+ * steps follow on it.  Returns once the host buffers have been read (the
+ * caller may reuse them); the steps may still be running.  Other grids,
+ * pageable host memory or n = 0: the two calls in sequence.  Errors as
+ * pf_set_fields and pf_step. */
+int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void* cl, int where,
+                       int64_t n);
 
 /* Discrete free energy of Eq. model1.1 for the current state, FP64:
  *   F_h = dV sum_i [H f_dw(phi_i) + p_i f_s,i + (1-p_i) f_l,i]

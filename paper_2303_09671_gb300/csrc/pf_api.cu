@@ -1,5 +1,6 @@
 // pf_api.cu -- the extern "C" boundary of libpf (declared in include/pf.h):
 // validation, device state, stream-ordered stepping and diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -22,7 +23,12 @@ struct pf_handle {
     double* hres = nullptr;      // pinned host results (4 doubles)
     double* drec = nullptr;      // per-step (F_h, S_h) records of pf_step_energies
     int64_t rec_cap = 0;
+    // pf_set_fields_step: a conversion stream, chunk streams, one event per slab
+    static constexpr int OV_STREAMS = 4;
+    cudaStream_t ov[OV_STREAMS] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ov_ev;
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
+    int ovchunk = 16;            // z planes per slab and CTA in pf_set_fields_step
     bool generic = false;        // run 2D / 3D through the generic kernel (cross-check)
     bool have_front = false;
     double last_xf = 0.0, last_t = 0.0;
@@ -32,6 +38,24 @@ struct pf_handle {
 namespace {
 
 thread_local std::string g_create_error;
+
+// Page-locked host memory is readable by a kernel itself (over NVLink-C2C or
+// PCIe): replace the three host pointers by their device views if all three
+// are page-locked; false (pointers unchanged) otherwise.
+bool device_views(const void* src[3]) {
+    const void* v[3];
+    for (int f = 0; f < 3; ++f) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, src[f]) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return false;
+        v[f] = at.devicePointer;
+    }
+    for (int f = 0; f < 3; ++f) src[f] = v[f];
+    return true;
+}
 
 int fail(pf_handle* h, int code, const std::string& msg) {
     if (h) h->err = msg;
@@ -163,6 +187,7 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     P.shift = params->shift ? 1 : 0;
     h->stream = static_cast<cudaStream_t>(stream);
     if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
+    if (const char* oc = std::getenv("PF_OVCHUNK")) h->ovchunk = std::atoi(oc);
     if (const char* g = std::getenv("PF_GENERIC")) h->generic = std::atoi(g) != 0;   // cross-check kernel
 
     const size_t bytes = (size_t)P.cells() * P.elem();
@@ -205,6 +230,9 @@ void pf_destroy(pf_handle* h) {
     if (h->dres) cudaFree(h->dres);
     if (h->hres) cudaFreeHost(h->hres);
     if (h->drec) cudaFree(h->drec);
+    for (cudaStream_t s : h->ov)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : h->ov_ev) cudaEventDestroy(ev);
     delete h;
 }
 
@@ -214,27 +242,7 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     const size_t bytes = (size_t)h->P.cells() * h->P.elem();
     const void* src[3] = {phi, cs, cl};
-    bool mapped = where == PF_HOST;
-    if (where == PF_HOST) {
-        // page-locked host memory is readable by the conversion kernel itself
-        // (over NVLink-C2C / PCIe): convert straight from it, without staging
-        for (int f = 0; f < 3 && mapped; ++f) {
-            cudaPointerAttributes at;
-            if (cudaPointerGetAttributes(&at, src[f]) != cudaSuccess) {
-                cudaGetLastError();
-                mapped = false;
-            } else if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) {
-                mapped = false;
-            } else {
-                src[f] = at.devicePointer;
-            }
-        }
-        if (!mapped) {
-            src[0] = phi;
-            src[1] = cs;
-            src[2] = cl;
-        }
-    }
+    const bool mapped = where == PF_HOST && device_views(src);
     if (where == PF_HOST && !mapped) {
         // stage (phi, c_s, c_l) in the idle ping-pong buffer, then convert
         const pf::Fields& st = h->buf[h->cur ^ 1];
@@ -254,6 +262,103 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     }
     return PF_OK;
+}
+
+int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void* cl, int where,
+                       int64_t n) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (n < 0) return fail(h, PF_EINVAL, "negative step count");
+    const pf::HostProblem& P = h->P;
+    const void* src[3] = {phi, cs, cl};
+    const bool readable = where == PF_DEVICE || device_views(src);
+    int zchunk = 0, nch = 0;
+    cudaError_t e = cudaSuccess;
+    if (P.dim == 3 && !h->generic && n > 0 && readable) {
+        // Short slabs: the last chunk of the first step, which can only start
+        // once the whole state is in, is then short too.  The extra halo planes
+        // they cost are computed while the SMs would otherwise wait on the link.
+        int req = h->ovchunk > 0 ? h->ovchunk : 16;
+        if (h->zchunk > 0) req = std::min(req, h->zchunk);
+        e = P.precision == 1 ? pf::step3d_chunks<double>(P, req, &zchunk, &nch)
+                             : pf::step3d_chunks<float>(P, req, &zchunk, &nch);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step setup");
+    }
+    if (nch < 2) {   // nothing to overlap: the two calls in sequence
+        int rc = pf_set_fields(h, phi, cs, cl, where);
+        return rc ? rc : pf_step(h, n);
+    }
+    // streams and per-slab events, made once per handle
+    for (int i = 0; i < pf_handle::OV_STREAMS && e == cudaSuccess; ++i)
+        if (!h->ov[i]) e = cudaStreamCreateWithFlags(&h->ov[i], cudaStreamNonBlocking);
+    while (e == cudaSuccess && (int)h->ov_ev.size() < nch + 1) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) h->ov_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream setup");
+    cudaStream_t conv = h->ov[0];
+    cudaEvent_t start = h->ov_ev[nch];
+    // Slab j (the planes of z-chunk j) is converted on `conv` after the work
+    // already queued on the handle's stream; chunk j of the first step starts
+    // once every plane it reads (z0 - 2 .. z1 + 1, wrapped on a periodic z
+    // axis) has been converted, on one of the chunk streams, so that the step
+    // of the first slabs runs while the later ones are still being read.
+    const long long plane = P.n[0] * P.n[1];
+    const int nz = (int)P.n[2];
+    int dev = 0, nsms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device query");
+    if (e == cudaSuccess) e = cudaEventRecord(start, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(conv, start, 0);
+    for (int j = 0; j < nch && e == cudaSuccess; ++j) {
+        const long long z0 = (long long)j * zchunk, z1 = std::min<long long>(nz, z0 + zchunk);
+        // two blocks per SM: the conversion is bound by the host link, and
+        // leaves the SMs to the step chunks that run beside it
+        e = pf::launch_to_state_range(P, src[0], src[1], src[2], h->buf[h->cur], z0 * plane,
+                                      (z1 - z0) * plane, 2 * nsms, conv);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ov_ev[j], conv);
+    }
+    const pf::Fields& in = h->buf[h->cur];
+    const pf::Fields& out = h->buf[h->cur ^ 1];
+    const bool zper = P.bc_lo[2] == PF_BC_PERIODIC;
+    for (int j = 0; j < nch && e == cudaSuccess; ++j) {
+        const int z0 = j * zchunk, z1 = std::min(nz, z0 + zchunk);
+        int need = std::min(nch - 1, std::min(nz - 1, z1 + 1) / zchunk);
+        if (zper && (z0 - 2 < 0 || z1 + 1 >= nz)) need = nch - 1;
+        cudaStream_t ks = h->ov[1 + j % (pf_handle::OV_STREAMS - 1)];
+        e = cudaStreamWaitEvent(ks, h->ov_ev[need], 0);
+        if (e != cudaSuccess) break;
+        pf::StepLaunch a;
+        a.prob = &P;
+        a.phi_in = in.phi; a.c_in = in.c; a.d_in = in.d; a.clo_in = in.clo; a.plo_in = in.plo;
+        a.phi_out = out.phi; a.c_out = out.c; a.d_out = out.d; a.clo_out = out.clo; a.plo_out = out.plo;
+        a.step = h->step;
+        a.shifts = h->shifts;
+        a.zchunk = zchunk;
+        a.zfirst = j;
+        a.zcount = 1;
+        a.use_generic = false;
+        a.stream = ks;
+        e = pf::launch_step(a);
+    }
+    // the handle's stream continues after every chunk
+    for (int i = 1; i < pf_handle::OV_STREAMS && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(start, h->ov[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, start, 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "overlapped upload and step");
+    h->have_front = false;
+    h->cur ^= 1;
+    h->step += 1;
+    if (where == PF_HOST) {
+        // the caller may reuse its host memory once the last slab is read
+        e = cudaEventSynchronize(h->ov_ev[nch - 1]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    }
+    return pf_step(h, n - 1);
 }
 
 int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {

@@ -40,11 +40,15 @@ struct StepLaunch {
     void *phi_out, *c_out, *d_out, *clo_out, *plo_out;
     int64_t step, shifts;   // clock of the input state
     int zchunk;             // planes per CTA along z (3D); <= 0: automatic
+    int zfirst = 0, zcount = 0;   // 3D: run z-chunks [zfirst, zfirst + zcount) only; zcount <= 0: all
     bool use_generic;       // 2D / 3D: the generic (1D/2D/3D) kernel instead of the paired one
     cudaStream_t stream;
 };
 
 cudaError_t launch_step(const StepLaunch& a);
+// the 3D step's z-chunk length and count for this problem (requested <= 0: automatic)
+template <typename T>
+cudaError_t step3d_chunks(const HostProblem& P, int requested, int* zchunk, int* nchunks);
 size_t step_smem_bytes(int precision, int dim);
 
 // Diagnostics.  `scratch` must hold diag_scratch_doubles(prob) doubles; results
@@ -63,6 +67,11 @@ cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& o
 // (phi, c_s, c_l) of the caller's precision <-> the device state (phi, c, d[, c_lo])
 cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* cs, const void* cl,
                             const Fields& out, cudaStream_t s);
+// the same for cells [first, first + count) only, on `blocks` blocks (<= 0: as
+// launch_to_state): one z-slab of a 3D grid, converted while earlier slabs step
+cudaError_t launch_to_state_range(const HostProblem& P, const void* phi, const void* cs, const void* cl,
+                                  const Fields& out, long long first, long long count, int blocks,
+                                  cudaStream_t s);
 void set_create_error(const std::string& msg);
 
 // One-time set-up of a kernel's launch attributes, per device: function

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(TX * (TY / 2), (sizeof(T) == 4 ? 2 : 1))
 step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
               const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
               T* __restrict__ d_out, T* __restrict__ clo_out, const PairConsts<typename Lanes<T>::V> K,
-              const GridConsts<T> G, int zchunk) {
+              const GridConsts<T> G, int zchunk, int zbase) {
     using L = PTile<T, TX, TY>;
     using V = typename L::V;
     using Q = typename L::Q;
@@ -405,7 +405,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         return (z == -1 && G.bc_lo[2] == BC_NOFLUX) || (z == nz - 1 && G.bc_hi[2] == BC_NOFLUX);
     };
 
-    const int z0 = blockIdx.z * zchunk;
+    const int z0 = (zbase + (int)blockIdx.z) * zchunk;   // this CTA's chunk of planes
     const int z1 = min(nz, z0 + zchunk);
     if (z0 >= z1) return;
 
@@ -537,6 +537,49 @@ static int choose_zchunk(long long tiles, int nz, long long resident) {
     return best;
 }
 
+// kernel attributes (once per device) and the occupancy the z-chunking plans with
+template <typename T>
+static cudaError_t step3d_setup(int* per_sm, int* sms) {
+    constexpr int TX = 32, TY = 16;
+    using L = PTile<T, TX, TY>;
+    static DeviceSetup setup;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(setup.mu);
+    if (!setup.done[dev]) {
+        decltype(&step3d_kernel<T, TX, TY, true, true>) kerns[4] = {
+            step3d_kernel<T, TX, TY, false, false>, step3d_kernel<T, TX, TY, false, true>,
+            step3d_kernel<T, TX, TY, true, false>, step3d_kernel<T, TX, TY, true, true>};
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+            e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+        if (e != cudaSuccess) return e;
+        int s = 1, p = 1;
+        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kerns[3], L::NT, L::BYTES);
+        setup.sms[dev] = s;
+        setup.per_sm[dev] = p < 1 ? 1 : p;
+        setup.done[dev] = true;
+    }
+    *per_sm = setup.per_sm[dev];
+    *sms = setup.sms[dev];
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t step3d_chunks(const HostProblem& P, int requested, int* zchunk, int* nchunks) {
+    int per_sm = 1, sms = 1;
+    cudaError_t e = step3d_setup<T>(&per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    const long long tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + 15) / 16);
+    int zc = requested;
+    if (zc <= 0) zc = choose_zchunk(tiles, (int)P.n[2], (long long)per_sm * sms);
+    *zchunk = zc;
+    *nchunks = (int)((P.n[2] + zc - 1) / zc);
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T>& Kc) {
     constexpr int TX = 32, TY = 16;
@@ -545,45 +588,30 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     decltype(&step3d_kernel<T, TX, TY, true, true>) kerns[2][2] = {
         {step3d_kernel<T, TX, TY, false, false>, step3d_kernel<T, TX, TY, false, true>},
         {step3d_kernel<T, TX, TY, true, false>, step3d_kernel<T, TX, TY, true, true>}};
-    static DeviceSetup setup;
-    int dev = 0, per_sm = 1, sms = 1;
-    {
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
-        std::lock_guard<std::mutex> lock(setup.mu);
-        if (!setup.done[dev]) {
-            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-                e = cudaFuncSetAttribute(kerns[i / 2][i % 2], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L::BYTES);
-            if (e != cudaSuccess) return e;
-            int s = 1, p = 1;
-            cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kerns[1][1], L::NT, L::BYTES);
-            setup.sms[dev] = s;
-            setup.per_sm[dev] = p < 1 ? 1 : p;
-            setup.done[dev] = true;
-        }
-        per_sm = setup.per_sm[dev];
-        sms = setup.sms[dev];
-    }
     const HostProblem& P = *a.prob;
+    int zchunk = 0, nchunks = 0;
+    cudaError_t e = step3d_chunks<T>(P, a.zchunk, &zchunk, &nchunks);
+    if (e != cudaSuccess) return e;
     const PairConsts<typename L::V> K = make_pair_consts<T>(P, C);
     const GridConsts<T> G = make_grid_consts<T>(P, Kc);
     dim3 block(L::NT);
     dim3 grid((C.n[0] + TX - 1) / TX, (C.n[1] + TY - 1) / TY, 1);
-    int zchunk = a.zchunk;
-    if (zchunk <= 0) zchunk = choose_zchunk((long long)grid.x * grid.y, C.n[2], (long long)per_sm * sms);
-    grid.z = (C.n[2] + zchunk - 1) / zchunk;
+    // all chunks, or chunks [zfirst, zfirst + zcount) only
+    const int zfirst = a.zcount > 0 ? a.zfirst : 0;
+    const int count = a.zcount > 0 ? std::min(a.zcount, nchunks - zfirst) : nchunks;
+    if (count <= 0) return cudaSuccess;
+    grid.z = count;
     auto kern = kerns[C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
-        static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk);
+        static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk, zfirst);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_step3d<float>(const StepLaunch&, const Consts<float>&, const Clock<float>&);
 template cudaError_t launch_step3d<double>(const StepLaunch&, const Consts<double>&, const Clock<double>&);
+template cudaError_t step3d_chunks<float>(const HostProblem&, int, int*, int*);
+template cudaError_t step3d_chunks<double>(const HostProblem&, int, int*, int*);
 
 }  // namespace pf

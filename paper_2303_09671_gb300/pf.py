@@ -93,6 +93,7 @@ _SIGS = {
     "pf_set_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "pf_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "pf_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "pf_set_fields_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int64]),
     "pf_energy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pf_step_energies": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "pf_solute_total": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
@@ -193,21 +194,30 @@ class Sim:
         self.stream = s
 
     # -- fields
-    def set_fields(self, phi, cs, cl):
+    def _field_ptrs(self, phi, cs, cl):
+        """(pointers, where, arrays kept alive) for CUDA tensors or host arrays."""
         if all(hasattr(a, "data_ptr") for a in (phi, cs, cl)):
             for a in (phi, cs, cl):
                 if not a.is_cuda or not a.is_contiguous() or tuple(a.shape) != self.shape:
                     raise ValueError("device fields must be contiguous CUDA tensors of the grid shape")
                 if a.element_size() != np.dtype(self.dtype).itemsize:
                     raise ValueError("device field dtype does not match the handle precision")
-            ptrs = [_VP(a.data_ptr()) for a in (phi, cs, cl)]
-            _check(lib().pf_set_fields(self._h, *ptrs, PF_DEVICE), self._h)
-            return
+            return [_VP(a.data_ptr()) for a in (phi, cs, cl)], PF_DEVICE, None
         arrs = [np.ascontiguousarray(a, dtype=self.dtype) for a in (phi, cs, cl)]
         for a in arrs:
             if a.shape != self.shape:
                 raise ValueError(f"field shape {a.shape} != {self.shape}")
-        _check(lib().pf_set_fields(self._h, *[_VP(a.ctypes.data) for a in arrs], PF_HOST), self._h)
+        return [_VP(a.ctypes.data) for a in arrs], PF_HOST, arrs
+
+    def set_fields(self, phi, cs, cl):
+        ptrs, where, _keep = self._field_ptrs(phi, cs, cl)
+        _check(lib().pf_set_fields(self._h, *ptrs, where), self._h)
+
+    def set_fields_step(self, phi, cs, cl, n: int = 1):
+        """set_fields then step(n), the upload overlapped with the first step
+        (3D, device or page-locked host fields)."""
+        ptrs, where, _keep = self._field_ptrs(phi, cs, cl)
+        _check(lib().pf_set_fields_step(self._h, *ptrs, where, int(n)), self._h)
 
     def get_fields(self, out=None):
         """Return (phi, cs, cl) as numpy arrays, or fill the given CUDA tensors."""

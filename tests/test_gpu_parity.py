@@ -343,6 +343,52 @@ def test_set_fields_from_pinned_host_memory(precision):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("zbc,zchunk,nz", [("noflux", None, 70), ("periodic", None, 70),
+                                          ("noflux", 1, 12), ("periodic", 2, 13), ("periodic", 3, 14)])
+def test_set_fields_step_equals_set_then_step(precision, zbc, zchunk, nz, monkeypatch):
+    """pf_set_fields_step (the upload converted slab by slab while the first
+    step's chunks run) leaves the same state, bit for bit, as pf_set_fields then
+    pf_step: from page-locked host memory, from device tensors and from pageable
+    memory (the sequential path), for one and for three steps, with z-chunks of
+    1, 2, 3 and the automatic length, on no-flux and periodic z axes."""
+    torch = pytest.importorskip("torch")
+    if zchunk is not None:
+        monkeypatch.setenv("PF_ZCHUNK", str(zchunk))
+    bc = ("noflux", "periodic", zbc)
+    # an x-y plane of 48 x 19 cells keeps every slab 16-byte aligned (the wide
+    # conversion); 45 x 19 does not (the scalar one)
+    nx = 48 if zchunk is None else 45
+    pr, phi, cs, cl = wl.random_state(3, (nx, 19, nz), dx=0.5, A=1.5, b=0.3, a=-0.3, seed=21,
+                                      bc_lo=bc, bc_hi=bc)
+    dt = np.float64 if precision == "fp64" else np.float32
+    host = [np.ascontiguousarray(a, dtype=dt) for a in (phi, cs, cl)]
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in host]
+    dev = [torch.from_numpy(a).cuda() for a in host]
+    for n in (1, 3):
+        with Sim(pr, precision) as s:
+            s.set_fields(*host)
+            s.step(n)
+            want = s.get_fields()
+            clock = s.clock
+        for src in (host, [p.numpy() for p in pinned], dev):
+            with Sim(pr, precision) as s:
+                s.step(0)
+                s.set_fields_step(*src, n=n)
+                got = s.get_fields()
+                assert s.clock == clock
+            for a, b in zip(want, got):
+                assert np.array_equal(a, b)
+        # a handle that has already stepped: the overlapped upload waits for it
+        with Sim(pr, precision) as s:
+            s.set_fields(*host)
+            s.step(4)
+            s.set_clock(0, 0)
+            s.set_fields_step(*[p.numpy() for p in pinned], n=n)
+            got = s.get_fields()
+        assert all(np.array_equal(a, b) for a, b in zip(want, got))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", ["planar1d", "pulled1d", "random3d"])
 def test_step_energies_match_per_call_energies(precision, case):
