@@ -298,7 +298,79 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
 
     // ---- C: faces.  Components 0..3 = phi, Y, mu_s, mu_l = (A.a, A.b, B.a, B.b).
-    // x face between halo cells hL and hL + 1 (ring index rL of hL) on plane z
+    // The cores take the records they read as arguments: the thread's own three
+    // faces share most of them, and each is then read from shared memory once.
+    // x face between halo cells L and R = L + 1: n = R - L; t1 (y) and t2 (z) =
+    // the sums of the two cells' centred differences, from the rows S, N and the
+    // planes M, P of both cells
+    auto xface_core = [&](const Q& aL, const Q& bL, const Q& aR, const Q& bR, const Q& aS, const Q& bS,
+                          const Q& aS1, const Q& bS1, const Q& aN, const Q& bN, const Q& aN1, const Q& bN1,
+                          const Q& aPL, const Q& bPL, const Q& aPR, const Q& bPR, const Q& aML, const Q& bML,
+                          const Q& aMR, const Q& bMR, const Q& cL, const Q& cR, const V dL, const V dR, V& Fc,
+                          V& Fd) {
+        V n[4] = {vsub(aR.a, aL.a), vsub(aR.b, aL.b), vsub(bR.a, bL.a), vsub(bR.b, bL.b)};
+        // y: the rows of a pair are its two lanes
+        V SP[4] = {vadd(aL.a, aR.a), vadd(aL.b, aR.b), vadd(bL.a, bR.a), vadd(bL.b, bR.b)};
+        V SS[4] = {vadd(aS.a, aS1.a), vadd(aS.b, aS1.b), vadd(bS.a, bS1.a), vadd(bS.b, bS1.b)};
+        V SN[4] = {vadd(aN.a, aN1.a), vadd(aN.b, aN1.b), vadd(bN.a, bN1.a), vadd(bN.b, bN1.b)};
+        V t1[4], t2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t1[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
+        t2[0] = vsub(vadd(aPL.a, aPR.a), vadd(aML.a, aMR.a));
+        t2[1] = vsub(vadd(aPL.b, aPR.b), vadd(aML.b, aMR.b));
+        t2[2] = vsub(vadd(bPL.a, bPR.a), vadd(bML.a, bMR.a));
+        t2[3] = vsub(vadd(bPL.b, bPR.b), vadd(bML.b, bMR.b));
+        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b), vadd(dL, dR), n,
+                               t1, t2, Fc, Fd);
+    };
+    // y faces above the two rows of the pair P (lanes: y+1/2 inside P, y+3/2
+    // between P and the pair N above): x differences from the E and W
+    // neighbours of P and N, z differences from the planes U (z+1) and D (z-1)
+    auto yface_core = [&](const Q& aP, const Q& bP, const Q& aN, const Q& bN, const Q& aPp, const Q& bPp,
+                          const Q& aPm, const Q& bPm, const Q& aNp, const Q& bNp, const Q& aNm, const Q& bNm,
+                          const Q& aPu, const Q& bPu, const Q& aPd, const Q& bPd, const Q& aNu, const Q& bNu,
+                          const Q& aNd, const Q& bNd, const Q& cP_, const Q& cN_, const V dP, const V dN, V& Fc,
+                          V& Fd) {
+        const V cP[4] = {aP.a, aP.b, bP.a, bP.b};
+        const V cN[4] = {aN.a, aN.b, bN.a, bN.b};
+        V n[4], t1[4], t2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) n[k] = vpair(cP[k].y - cP[k].x, cN[k].x - cP[k].y);
+        const V DP[4] = {vsub(aPp.a, aPm.a), vsub(aPp.b, aPm.b), vsub(bPp.a, bPm.a), vsub(bPp.b, bPm.b)};
+        const V DN[4] = {vsub(aNp.a, aNm.a), vsub(aNp.b, aNm.b), vsub(bNp.a, bNm.a), vsub(bNp.b, bNm.b)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t1[k] = vpair(DP[k].x + DP[k].y, DP[k].y + DN[k].x);
+        const V EP[4] = {vsub(aPu.a, aPd.a), vsub(aPu.b, aPd.b), vsub(bPu.a, bPd.a), vsub(bPu.b, bPd.b)};
+        const V EN[4] = {vsub(aNu.a, aNd.a), vsub(aNu.b, aNd.b), vsub(bNu.a, bNd.a), vsub(bNu.b, bNd.b)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t2[k] = vpair(EP[k].x + EP[k].y, EP[k].y + EN[k].x);
+        const V f = vmul(vlit<V>(0.5), vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
+        const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
+        const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
+        face_flux<V, true, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
+    };
+    // z face between the cell 0 on plane z and the cell 1 on plane z+1: x and y
+    // differences from the E/W (p/m) and N/S neighbours on both planes
+    auto zface_core = [&](const Q& a0, const Q& b0, const Q& a1, const Q& b1, const Q& ap0, const Q& bp0,
+                          const Q& am0, const Q& bm0, const Q& ap1, const Q& bp1, const Q& am1, const Q& bm1,
+                          const Q& aS0, const Q& bS0, const Q& aS1, const Q& bS1, const Q& aN0, const Q& bN0,
+                          const Q& aN1, const Q& bN1, const Q& c0, const Q& c1, const V d0, const V d1, V& Fc,
+                          V& Fd) {
+        V n[4] = {vsub(a1.a, a0.a), vsub(a1.b, a0.b), vsub(b1.a, b0.a), vsub(b1.b, b0.b)};
+        V t1[4], t2[4];
+        t1[0] = vsub(vadd(ap0.a, ap1.a), vadd(am0.a, am1.a));
+        t1[1] = vsub(vadd(ap0.b, ap1.b), vadd(am0.b, am1.b));
+        t1[2] = vsub(vadd(bp0.a, bp1.a), vadd(bm0.a, bm1.a));
+        t1[3] = vsub(vadd(bp0.b, bp1.b), vadd(bm0.b, bm1.b));
+        const V SP[4] = {vadd(a0.a, a1.a), vadd(a0.b, a1.b), vadd(b0.a, b1.a), vadd(b0.b, b1.b)};
+        const V SS[4] = {vadd(aS0.a, aS1.a), vadd(aS0.b, aS1.b), vadd(bS0.a, bS1.a), vadd(bS0.b, bS1.b)};
+        const V SN[4] = {vadd(aN0.a, aN1.a), vadd(aN0.b, aN1.b), vadd(bN0.a, bN1.a), vadd(bN0.b, bN1.b)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t2[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
+        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
+                               vadd(d0, d1), n, t1, t2, Fc, Fd);
+    };
+    // single faces (the tile's low x and low y edges, the z face below the chunk)
     auto xface = [&](int z, int hL, int rL, V& Fc, V& Fd) {
         const Q* A0 = sA + (z & 3) * HP;
         const Q* AM = sA + ((z - 1) & 3) * HP;
@@ -309,28 +381,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const Q* C0 = sC + slot3(z) * HP;
         const V* D0 = sD + (z & 1) * RP;
         const int hR = hL + 1;
-        const Q aL = A0[hL], aR = A0[hR], bL = B0[hL], bR = B0[hR];
-        V n[4] = {vsub(aR.a, aL.a), vsub(aR.b, aL.b), vsub(bR.a, bL.a), vsub(bR.b, bL.b)};
-        // y: the rows of a pair are its two lanes
-        const Q aS = A0[hL - HX], aS1 = A0[hR - HX], aN = A0[hL + HX], aN1 = A0[hR + HX];
-        const Q bS = B0[hL - HX], bS1 = B0[hR - HX], bN = B0[hL + HX], bN1 = B0[hR + HX];
-        V SP[4] = {vadd(aL.a, aR.a), vadd(aL.b, aR.b), vadd(bL.a, bR.a), vadd(bL.b, bR.b)};
-        V SS[4] = {vadd(aS.a, aS1.a), vadd(aS.b, aS1.b), vadd(bS.a, bS1.a), vadd(bS.b, bS1.b)};
-        V SN[4] = {vadd(aN.a, aN1.a), vadd(aN.b, aN1.b), vadd(bN.a, bN1.a), vadd(bN.b, bN1.b)};
-        V t1[4], t2[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t1[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
-        const Q aPL = AP[hL], aPR = AP[hR], aML = AM[hL], aMR = AM[hR];
-        const Q bPL = BP[hL], bPR = BP[hR], bML = BM[hL], bMR = BM[hR];
-        t2[0] = vsub(vadd(aPL.a, aPR.a), vadd(aML.a, aMR.a));
-        t2[1] = vsub(vadd(aPL.b, aPR.b), vadd(aML.b, aMR.b));
-        t2[2] = vsub(vadd(bPL.a, bPR.a), vadd(bML.a, bMR.a));
-        t2[3] = vsub(vadd(bPL.b, bPR.b), vadd(bML.b, bMR.b));
-        const Q cL = C0[hL], cR = C0[hR];
-        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b),
-                  vadd(D0[rL], D0[rL + 1]), n, t1, t2, Fc, Fd);
+        xface_core(A0[hL], B0[hL], A0[hR], B0[hR], A0[hL - HX], B0[hL - HX], A0[hR - HX], B0[hR - HX], A0[hL + HX],
+                   B0[hL + HX], A0[hR + HX], B0[hR + HX], AP[hL], BP[hL], AP[hR], BP[hR], AM[hL], BM[hL], AM[hR],
+                   BM[hR], C0[hL], C0[hR], D0[rL], D0[rL + 1], Fc, Fd);
     };
-    // y faces above the two rows of the pair at hL: lanes (y+1/2, y+3/2)
     auto yface = [&](int z, int hL, int rL, V& Fc, V& Fd) {
         const Q* A0 = sA + (z & 3) * HP;
         const Q* AM = sA + ((z - 1) & 3) * HP;
@@ -341,33 +395,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const Q* C0 = sC + slot3(z) * HP;
         const V* D0 = sD + (z & 1) * RP;
         const int hN = hL + HX;
-        const Q aP = A0[hL], aN = A0[hN], bP = B0[hL], bN = B0[hN];
-        const V cP[4] = {aP.a, aP.b, bP.a, bP.b};
-        const V cN[4] = {aN.a, aN.b, bN.a, bN.b};
-        V n[4], t1[4], t2[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) n[k] = vpair(cP[k].y - cP[k].x, cN[k].x - cP[k].y);
-        // x: differences at both pairs, then the two rows of each face
-        const Q aPp = A0[hL + 1], aPm = A0[hL - 1], aNp = A0[hN + 1], aNm = A0[hN - 1];
-        const Q bPp = B0[hL + 1], bPm = B0[hL - 1], bNp = B0[hN + 1], bNm = B0[hN - 1];
-        const V DP[4] = {vsub(aPp.a, aPm.a), vsub(aPp.b, aPm.b), vsub(bPp.a, bPm.a), vsub(bPp.b, bPm.b)};
-        const V DN[4] = {vsub(aNp.a, aNm.a), vsub(aNp.b, aNm.b), vsub(bNp.a, bNm.a), vsub(bNp.b, bNm.b)};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t1[k] = vpair(DP[k].x + DP[k].y, DP[k].y + DN[k].x);
-        const Q aPu = AP[hL], aPd = AM[hL], aNu = AP[hN], aNd = AM[hN];
-        const Q bPu = BP[hL], bPd = BM[hL], bNu = BP[hN], bNd = BM[hN];
-        const V EP[4] = {vsub(aPu.a, aPd.a), vsub(aPu.b, aPd.b), vsub(bPu.a, bPd.a), vsub(bPu.b, bPd.b)};
-        const V EN[4] = {vsub(aNu.a, aNd.a), vsub(aNu.b, aNd.b), vsub(bNu.a, bNd.a), vsub(bNu.b, bNd.b)};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t2[k] = vpair(EP[k].x + EP[k].y, EP[k].y + EN[k].x);
-        const Q cP_ = C0[hL], cN_ = C0[hN];
-        const V dP = D0[rL], dN = D0[rL + RX];
-        const V f = vmul(vlit<V>(0.5), vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
-        const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
-        const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
-        face_flux<V, true, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
+        yface_core(A0[hL], B0[hL], A0[hN], B0[hN], A0[hL + 1], B0[hL + 1], A0[hL - 1], B0[hL - 1], A0[hN + 1],
+                   B0[hN + 1], A0[hN - 1], B0[hN - 1], AP[hL], BP[hL], AM[hL], BM[hL], AP[hN], BP[hN], AM[hN],
+                   BM[hN], C0[hL], C0[hN], D0[rL], D0[rL + RX], Fc, Fd);
     };
-    // z face between planes z and z+1 of the pair at h (ring index r)
     auto zface = [&](int z, int h, int r, V& Fc, V& Fd) {
         const Q* A0 = sA + (z & 3) * HP;
         const Q* A1 = sA + ((z + 1) & 3) * HP;
@@ -377,29 +408,37 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const Q* C1 = sC + slot3(z + 1) * HP;
         const V* D0 = sD + (z & 1) * RP;
         const V* D1 = sD + ((z + 1) & 1) * RP;
-        const Q a0 = A0[h], a1 = A1[h], b0 = B0[h], b1 = B1[h];
-        V n[4] = {vsub(a1.a, a0.a), vsub(a1.b, a0.b), vsub(b1.a, b0.a), vsub(b1.b, b0.b)};
-        V t1[4], t2[4];
-        {
-            const Q ap0 = A0[h + 1], am0 = A0[h - 1], ap1 = A1[h + 1], am1 = A1[h - 1];
-            const Q bp0 = B0[h + 1], bm0 = B0[h - 1], bp1 = B1[h + 1], bm1 = B1[h - 1];
-            t1[0] = vsub(vadd(ap0.a, ap1.a), vadd(am0.a, am1.a));
-            t1[1] = vsub(vadd(ap0.b, ap1.b), vadd(am0.b, am1.b));
-            t1[2] = vsub(vadd(bp0.a, bp1.a), vadd(bm0.a, bm1.a));
-            t1[3] = vsub(vadd(bp0.b, bp1.b), vadd(bm0.b, bm1.b));
-        }
-        {
-            const Q aS0 = A0[h - HX], aS1 = A1[h - HX], aN0 = A0[h + HX], aN1 = A1[h + HX];
-            const Q bS0 = B0[h - HX], bS1 = B1[h - HX], bN0 = B0[h + HX], bN1 = B1[h + HX];
-            const V SP[4] = {vadd(a0.a, a1.a), vadd(a0.b, a1.b), vadd(b0.a, b1.a), vadd(b0.b, b1.b)};
-            const V SS[4] = {vadd(aS0.a, aS1.a), vadd(aS0.b, aS1.b), vadd(bS0.a, bS1.a), vadd(bS0.b, bS1.b)};
-            const V SN[4] = {vadd(aN0.a, aN1.a), vadd(aN0.b, aN1.b), vadd(bN0.a, bN1.a), vadd(bN0.b, bN1.b)};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) t2[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
-        }
-        const Q c0 = C0[h], c1 = C1[h];
-        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
-                  vadd(D0[r], D1[r]), n, t1, t2, Fc, Fd);
+        zface_core(A0[h], B0[h], A1[h], B1[h], A0[h + 1], B0[h + 1], A0[h - 1], B0[h - 1], A1[h + 1], B1[h + 1],
+                   A1[h - 1], B1[h - 1], A0[h - HX], B0[h - HX], A1[h - HX], B1[h - HX], A0[h + HX], B0[h + HX],
+                   A1[h + HX], B1[h + HX], C0[h], C1[h], D0[r], D1[r], Fc, Fd);
+    };
+    // the own pair's x, y and z faces on plane z: 32 records of {phi, Y} and
+    // {mu_s, mu_l}, 4 of {c_s, c_l} and 4 rates, each read once
+    auto own_faces = [&](int z, V& Fxc, V& Fxd, V& Fyc, V& Fyd, V& Fzc, V& Fzd) {
+        const int h = own_h, r = own_r;
+        const Q* A0 = sA + (z & 3) * HP;
+        const Q* AM = sA + ((z - 1) & 3) * HP;
+        const Q* AP = sA + ((z + 1) & 3) * HP;
+        const Q* B0 = sB + (z & 3) * HP;
+        const Q* BM = sB + ((z - 1) & 3) * HP;
+        const Q* BP = sB + ((z + 1) & 3) * HP;
+        const Q* C0 = sC + slot3(z) * HP;
+        const V* D0 = sD + (z & 1) * RP;
+        // plane z: the pair O, its x neighbours E, W, the pairs N, S and NE, SE, NW
+        const Q aO = A0[h], bO = B0[h], aE = A0[h + 1], bE = B0[h + 1], aW = A0[h - 1], bW = B0[h - 1];
+        const Q aN = A0[h + HX], bN = B0[h + HX], aS = A0[h - HX], bS = B0[h - HX];
+        const Q aNE = A0[h + HX + 1], bNE = B0[h + HX + 1];
+        // plane z+1 (U) and z-1 (D)
+        const Q aU = AP[h], bU = BP[h], aUE = AP[h + 1], bUE = BP[h + 1], aUN = AP[h + HX], bUN = BP[h + HX];
+        const Q aD = AM[h], bD = BM[h];
+        const Q cO = C0[h];
+        const V dO = D0[r];
+        xface_core(aO, bO, aE, bE, aS, bS, A0[h - HX + 1], B0[h - HX + 1], aN, bN, aNE, bNE, aU, bU, aUE, bUE, aD,
+                   bD, AM[h + 1], BM[h + 1], cO, C0[h + 1], dO, D0[r + 1], Fxc, Fxd);
+        yface_core(aO, bO, aN, bN, aE, bE, aW, bW, aNE, bNE, A0[h + HX - 1], B0[h + HX - 1], aU, bU, aD, bD, aUN,
+                   bUN, AM[h + HX], BM[h + HX], cO, C0[h + HX], dO, D0[r + RX], Fyc, Fyd);
+        zface_core(aO, bO, aU, bU, aE, bE, aW, bW, aUE, bUE, AP[h - 1], BP[h - 1], aS, bS, AP[h - HX], BP[h - HX],
+                   aN, bN, aUN, bUN, cO, sC[slot3(z + 1) * HP + h], dO, sD[((z + 1) & 1) * RP + r], Fzc, Fzd);
     };
     auto z_noflux = [&](int z) {
         return (z == -1 && G.bc_lo[2] == BC_NOFLUX) || (z == nz - 1 && G.bc_hi[2] == BC_NOFLUX);
@@ -491,9 +530,13 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         fetch_own(k);
         cp_async_commit();
         rates_plane(k + 1);
-        xface(k, own_h, own_r, fxc, fxd);
-        yface(k, own_h, own_r, fyc, fyd);
-        zface(k, own_h, own_r, fzc, fzd);
+        if constexpr (sizeof(T) == 4) {
+            own_faces(k, fxc, fxd, fyc, fyd, fzc, fzd);
+        } else {   // FP64: one face at a time keeps fewer registers live
+            xface(k, own_h, own_r, fxc, fxd);
+            yface(k, own_h, own_r, fyc, fyd);
+            zface(k, own_h, own_r, fzc, fzd);
+        }
         if (nf_x) fxc = fxd = vpair(T(0), T(0));
         fyc = vmask(fyc, nf_ylo, nf_yhi);
         fyd = vmask(fyd, nf_ylo, nf_yhi);
