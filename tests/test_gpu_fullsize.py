@@ -64,6 +64,26 @@ def test_sphere_256_cubed(sphere256, precision):
     check(pr, st, g, precision)
 
 
+def test_sphere_256_cubed_overlapped_upload(sphere256):
+    """The end-to-end path the benchmark times: pf_set_fields_step from
+    page-locked host memory (16-plane slabs converted while the first step's
+    chunks run) leaves the 256^3 state bit for bit equal to pf_set_fields then
+    pf_step, which the test above holds to the oracle."""
+    torch = pytest.importorskip("torch")
+    pr, phi, cs, cl = sphere256
+    f32 = [np.ascontiguousarray(a, dtype=np.float32) for a in (phi, cs, cl)]
+    pinned = [torch.from_numpy(a).pin_memory() for a in f32]
+    with Sim(pr, "fp32") as s:
+        s.set_fields(*f32)
+        s.step(2)
+        want = s.get_fields()
+    with Sim(pr, "fp32") as s:
+        s.set_fields_step(*[p.numpy() for p in pinned], n=2)
+        got = s.get_fields()
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_perturbed_front_1024_squared(precision):
     pr, phi, cs, cl = wl.perturbed_front_2d(A=1.0, b=1.0)
