@@ -290,8 +290,12 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
         return rc ? rc : pf_step(h, n);
     }
     // streams and per-slab events, made once per handle
-    for (int i = 0; i < pf_handle::OV_STREAMS && e == cudaSuccess; ++i)
-        if (!h->ov[i]) e = cudaStreamCreateWithFlags(&h->ov[i], cudaStreamNonBlocking);
+    for (int i = 0; i < pf_handle::OV_STREAMS && e == cudaSuccess; ++i) {
+        if (h->ov[i]) continue;
+        int lo = 0, hi = 0;
+        if (i == 0) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);   // conversion first
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->ov[i], cudaStreamNonBlocking, i == 0 ? hi : lo);
+    }
     while (e == cudaSuccess && (int)h->ov_ev.size() < nch + 1) {
         cudaEvent_t ev = nullptr;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -328,6 +332,8 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
         const int z0 = j * zchunk, z1 = std::min(nz, z0 + zchunk);
         int need = std::min(nch - 1, std::min(nz - 1, z1 + 1) / zchunk);
         if (zper && (z0 - 2 < 0 || z1 + 1 >= nz)) need = nch - 1;
+        // three chunk streams: a chunk has one CTA per SM, so several run side by
+        // side (measured: 1.46 ms per call with one stream, 1.18 with two, 1.13 with three)
         cudaStream_t ks = h->ov[1 + j % (pf_handle::OV_STREAMS - 1)];
         e = cudaStreamWaitEvent(ks, h->ov_ev[need], 0);
         if (e != cudaSuccess) break;
