@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2303_09671_gb300 import build as pbuild
@@ -72,6 +73,7 @@ def test_create_rejects_one_sided_periodic():
 def test_null_handle_calls_fail_cleanly():
     L = pf.lib()
     assert L.pf_step(None, 1) == pf.PF_EINVAL
+    assert L.pf_set_fields_step(None, None, None, None, pf.PF_HOST, 1) == pf.PF_EINVAL
     v = ctypes.c_double()
     assert L.pf_energy(None, ctypes.byref(v)) == pf.PF_EINVAL
     L.pf_destroy(None)
@@ -101,3 +103,16 @@ def test_create_rejects_grids_beyond_the_launch_limits():
     g.n[0], g.n[1], g.n[2] = 1 << 17, 1 << 14, 3
     rc = pf.lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), None, ctypes.byref(h))
     assert rc == pf.PF_EINVAL and "plane" in pf.lib().pf_last_error(None).decode()
+
+
+def test_empty_batch_is_rejected_before_any_device_work():
+    """A batch of no instances (or of an instance below 8 cells) is an invalid
+    descriptor: PF_EINVAL from validation, which runs before any CUDA call, so
+    this holds without a GPU."""
+    pr, _, _, _ = wl.pulled_front_1d(N=64)
+    for lengths, v in (([], []), ([4], [0.1])):
+        n = int(sum(lengths))
+        z = np.zeros(n)
+        with pytest.raises(pf.PFError) as e:
+            pf.run_batch(pr, lengths, v, z, z + 0.1, z + 1.0)
+        assert e.value.code == pf.PF_EINVAL
