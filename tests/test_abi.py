@@ -108,11 +108,22 @@ def test_create_rejects_grids_beyond_the_launch_limits():
 def test_empty_batch_is_rejected_before_any_device_work():
     """A batch of no instances (or of an instance below 8 cells) is an invalid
     descriptor: PF_EINVAL from validation, which runs before any CUDA call, so
-    this holds without a GPU."""
+    this holds through the C ABI without a GPU."""
+    L = pf.lib()
     pr, _, _, _ = wl.pulled_front_1d(N=64)
-    for lengths, v in (([], []), ([4], [0.1])):
-        n = int(sum(lengths))
-        z = np.zeros(n)
-        with pytest.raises(pf.PFError) as e:
-            pf.run_batch(pr, lengths, v, z, z + 0.1, z + 1.0)
-        assert e.value.code == pf.PF_EINVAL
+    g, b, p = pf.make_structs(dict(pr, n=(8,), shift=False, v_pull=0.0), "fp32")
+    for lengths in ([], [4]):
+        n = np.ascontiguousarray(lengths if lengths else [0], dtype=np.int64)
+        v = np.full(max(1, len(lengths)), 0.1)
+        z = np.zeros(64, dtype=np.float32)
+        D = pf.pf_batch_desc()
+        D.n_instances = len(lengths)
+        D.n = n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        D.v_pull = v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        D.phi0 = D.cs0 = D.cl0 = z.ctypes.data
+        D.dx = float(pr["dx"])
+        D.bc = b
+        D.params = p
+        D.max_steps, D.steps_per_launch, D.launches_per_graph = 100, 10, 1
+        R = pf.pf_batch_result()
+        assert L.pf_run_batch(ctypes.byref(D), ctypes.byref(R), None) == pf.PF_EINVAL
