@@ -223,9 +223,8 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
 
     // ---- B: dx^2 phidot of one ring pair cell of plane z -> sD[z & 1][r]
-    auto rate_cell = [&](int z, int dsc, T xc, int r) {
+    auto rate_of = [&](int z, int dsc, T xc) -> V {
         const bool ghost_z = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) < 0;
-        V* D = sD + (z & 1) * RP;
         const V* P0 = sP + slot3(z) * HP;
         const V* PM = sP + slot3(z - 1) * HP;
         const V* PP = sP + slot3(z + 1) * HP;
@@ -290,8 +289,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V R = vfma(K.sigma, lap, vmul(K.dx2, vsub(anti, vfma(K.H, dfdw, vmul(dG, dp)))));
             pd = vmask(vmul(R, vrcp(Kc)), (dsc >> 12) & 1, (dsc >> 13) & 1);
         }
-        D[r] = pd;
+        return pd;
     };
+    auto rate_cell = [&](int z, int dsc, T xc, int r) { sD[(z & 1) * RP + r] = rate_of(z, dsc, xc); };
     auto rates_plane = [&](int z) {
         rate_cell(z, own_dsc, own_xc, own_r);
         if (bor_r >= 0) rate_cell(z, bor_dsc, bor_xc, bor_r);
@@ -414,7 +414,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
     // the own pair's x, y and z faces on plane z: 32 records of {phi, Y} and
     // {mu_s, mu_l}, 4 of {c_s, c_l} and 4 rates, each read once
-    auto own_faces = [&](int z, V& Fxc, V& Fxd, V& Fyc, V& Fyd, V& Fzc, V& Fzd) {
+    auto own_faces = [&](int z, const V rate_up, V& Fxc, V& Fxd, V& Fyc, V& Fyd, V& Fzc, V& Fzd) {
         const int h = own_h, r = own_r;
         const Q* A0 = sA + (z & 3) * HP;
         const Q* AM = sA + ((z - 1) & 3) * HP;
@@ -438,7 +438,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         yface_core(aO, bO, aN, bN, aE, bE, aW, bW, aNE, bNE, A0[h + HX - 1], B0[h + HX - 1], aU, bU, aD, bD, aUN,
                    bUN, AM[h + HX], BM[h + HX], cO, C0[h + HX], dO, D0[r + RX], Fyc, Fyd);
         zface_core(aO, bO, aU, bU, aE, bE, aW, bW, aUE, bUE, AP[h - 1], BP[h - 1], aS, bS, AP[h - HX], BP[h - HX],
-                   aN, bN, aUN, bUN, cO, sC[slot3(z + 1) * HP + h], dO, sD[((z + 1) & 1) * RP + r], Fzc, Fzd);
+                   aN, bN, aUN, bUN, cO, sC[slot3(z + 1) * HP + h], dO, rate_up, Fzc, Fzd);
     };
     auto z_noflux = [&](int z) {
         return (z == -1 && G.bc_lo[2] == BC_NOFLUX) || (z == nz - 1 && G.bc_hi[2] == BC_NOFLUX);
@@ -529,10 +529,16 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         if (k + 1 < z1) fetch_plane(k + 3);
         fetch_own(k);
         cp_async_commit();
-        rates_plane(k + 1);
         if constexpr (sizeof(T) == 4) {
-            own_faces(k, fxc, fxd, fyc, fyd, fzc, fzd);
+            // The own rate of plane k+1 goes to the z face in a register and to
+            // shared memory only after the faces: with no shared store between
+            // them, the records the rate and the faces both read are read once.
+            const V rate_up = rate_of(k + 1, own_dsc, own_xc);
+            own_faces(k, rate_up, fxc, fxd, fyc, fyd, fzc, fzd);
+            sD[((k + 1) & 1) * RP + own_r] = rate_up;
+            if (bor_r >= 0) rate_cell(k + 1, bor_dsc, bor_xc, bor_r);
         } else {   // FP64: one face at a time keeps fewer registers live
+            rates_plane(k + 1);
             xface(k, own_h, own_r, fxc, fxd);
             yface(k, own_h, own_r, fyc, fyd);
             zface(k, own_h, own_r, fzc, fzd);
