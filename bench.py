@@ -65,10 +65,10 @@ SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 # of the kernel's device code the capture ran.  The figure is reported as null
 # as soon as those sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.332032e6 + 228.005888e6) / 256 ** 3,
+    "bytes_per_cell_update": (280.543744e6 + 228.566016e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh"),
-    "sha256": ("d62eee374f1b76cfeef51283dcfc22a8007e2190518d68bb608ef973b8cace91",
+    "sha256": ("bcc4cc8026c96a54a566476cd9b6003b19d081729202abd224acc16eced012e3",
                "ca8a8936b55cf3a8d7bbbc6ef71bd5cec65b4f4c0f6931f1105397cc5e2714b8",
                "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60"),
 }

@@ -414,7 +414,8 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
     // the own pair's x, y and z faces on plane z: 32 records of {phi, Y} and
     // {mu_s, mu_l}, 4 of {c_s, c_l} and 4 rates, each read once
-    auto own_faces = [&](int z, const V rate_up, V& Fxc, V& Fxd, V& Fyc, V& Fyd, V& Fzc, V& Fzd) {
+    auto own_faces = [&](int z, const V rate_here, const V rate_up, V& phi_here, V& Fxc, V& Fxd, V& Fyc, V& Fyd,
+                         V& Fzc, V& Fzd) {
         const int h = own_h, r = own_r;
         const Q* A0 = sA + (z & 3) * HP;
         const Q* AM = sA + ((z - 1) & 3) * HP;
@@ -432,7 +433,8 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const Q aU = AP[h], bU = BP[h], aUE = AP[h + 1], bUE = BP[h + 1], aUN = AP[h + HX], bUN = BP[h + HX];
         const Q aD = AM[h], bD = BM[h];
         const Q cO = C0[h];
-        const V dO = D0[r];
+        const V dO = rate_here;
+        phi_here = aO.a;
         xface_core(aO, bO, aE, bE, aS, bS, A0[h - HX + 1], B0[h - HX + 1], aN, bN, aNE, bNE, aU, bU, aUE, bUE, aD,
                    bD, AM[h + 1], BM[h + 1], cO, C0[h + 1], dO, D0[r + 1], Fxc, Fxd);
         yface_core(aO, bO, aN, bN, aE, bE, aW, bW, aNE, bNE, A0[h + HX - 1], B0[h + HX - 1], aU, bU, aD, bD, aUN,
@@ -475,6 +477,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 
     // fluxes of the plane being updated, carried from its faces phase to its update
     V fxc = vlit<V>(0.0), fxd = fxc, fyc = fxc, fyd = fxc, fzc = fxc, fzd = fxc;
+    // FP32: the own pair's rate and phi carried in registers from the plane
+    // loop to the update (the rate of plane k is computed while plane k-1 is
+    // faced, read by the z face of k and by the update of k)
+    V rate_k = sD[(z0 & 1) * RP + own_r], rate_prev = fxc, phi_prev = fxc;
     // update of plane k from its fluxes and the own-cell state staged in sO
     auto update = [&](int k) {
         const Q left = sFx[ty * FXP + tx];
@@ -483,7 +489,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V dFc = vadd(vadd(vsub(fxc, left.a), vpair(fyc.x - bc_, fyc.y - fyc.x)), vsub(fzc, fzc_down));
         const V dFd = vadd(vadd(vsub(fxd, left.b), vpair(fyd.x - bd_, fyd.y - fyd.x)), vsub(fzd, fzd_down));
         const V c_k = vpair(sO[tid], sO[NT + tid]), d_k = vpair(sO[2 * NT + tid], sO[3 * NT + tid]);
-        const V phi_new = vfma(K.dt_dx2, sD[(k & 1) * RP + own_r], sA[(k & 3) * HP + own_h].a);
+        V phi_new;
+        if constexpr (sizeof(T) == 4) phi_new = vfma(K.dt_dx2, rate_prev, phi_prev);
+        else phi_new = vfma(K.dt_dx2, sD[(k & 1) * RP + own_r], sA[(k & 3) * HP + own_h].a);
         const V d_new = vfma(K.dt_dx2, dFd, d_k);
         const V dcv = vmul(K.dt_dx2, dFc);
         V c_new, lo_new;
@@ -534,9 +542,13 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             // shared memory only after the faces: with no shared store between
             // them, the records the rate and the faces both read are read once.
             const V rate_up = rate_of(k + 1, own_dsc, own_xc);
-            own_faces(k, rate_up, fxc, fxd, fyc, fyd, fzc, fzd);
+            V phi_k;
+            own_faces(k, rate_k, rate_up, phi_k, fxc, fxd, fyc, fyd, fzc, fzd);
             sD[((k + 1) & 1) * RP + own_r] = rate_up;
             if (bor_r >= 0) rate_cell(k + 1, bor_dsc, bor_xc, bor_r);
+            rate_prev = rate_k;
+            phi_prev = phi_k;
+            rate_k = rate_up;
         } else {   // FP64: one face at a time keeps fewer registers live
             rates_plane(k + 1);
             xface(k, own_h, own_r, fxc, fxd);
