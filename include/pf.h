@@ -156,8 +156,10 @@ int pf_step(pf_handle* h, int64_t n);
  * transfer.  The handle's stream waits for all of it; the remaining n - 1
  * steps follow on it.  Returns once the host buffers have been read (the
  * caller may reuse them); the steps may still be running.  Other grids,
- * pageable host memory or n = 0: the two calls in sequence.  Errors as
- * pf_set_fields and pf_step. */
+ * pageable host memory or n = 0: the two calls in sequence.  The handle
+ * creates its internal streams and events on first use and frees them in
+ * pf_destroy.  Errors as pf_set_fields and pf_step; after PF_ECUDA the state
+ * is undefined until the next pf_set_fields. */
 int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void* cl, int where,
                        int64_t n);
 
