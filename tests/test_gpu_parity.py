@@ -389,6 +389,39 @@ def test_set_fields_step_equals_set_then_step(precision, zbc, zchunk, nz, monkey
         assert all(np.array_equal(a, b) for a, b in zip(want, got))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_set_fields_step_back_to_back(precision):
+    """Two overlapped uploads queued without a host wait in between (a second
+    state converted into the buffer the first call's step writes, and stepped
+    into the buffer it reads) leave the state that set_fields + step of the
+    second state leaves, bit for bit; so does a third call after more steps."""
+    torch = pytest.importorskip("torch")
+    dt = np.float64 if precision == "fp64" else np.float32
+    bc = ("noflux", "periodic", "periodic")
+    states = []
+    for seed in (31, 32):
+        pr, phi, cs, cl = wl.random_state(3, (48, 19, 70), dx=0.5, A=1.5, b=0.3, a=-0.3, seed=seed,
+                                          bc_lo=bc, bc_hi=bc)
+        states.append([torch.from_numpy(np.ascontiguousarray(x, dtype=dt)).pin_memory() for x in (phi, cs, cl)])
+    want = []
+    for st in states:
+        with Sim(pr, precision) as s:
+            s.set_fields(*[x.numpy() for x in st])
+            s.step(1)
+            want.append(s.get_fields())
+    with Sim(pr, precision) as s:
+        s.set_fields_step(*[x.numpy() for x in states[0]], n=1)
+        s.set_clock(0, 0)
+        s.set_fields_step(*[x.numpy() for x in states[1]], n=1)
+        got = s.get_fields()
+        assert all(np.array_equal(a, b) for a, b in zip(want[1], got))
+        s.step(5)
+        s.set_clock(0, 0)
+        s.set_fields_step(*[x.numpy() for x in states[0]], n=1)
+        got = s.get_fields()
+        assert all(np.array_equal(a, b) for a, b in zip(want[0], got))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", ["planar1d", "pulled1d", "random3d"])
 def test_step_energies_match_per_call_energies(precision, case):
