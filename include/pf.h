@@ -185,6 +185,14 @@ int pf_step_energies(pf_handle* h, int64_t n, double* F);
  * Synchronises the stream. */
 int pf_solute_total(pf_handle* h, double* S);
 
+/* pf_solute_total without the wait: the reduction and the copy of S_h into *S
+ * (page-locked host memory for the copy to be asynchronous; the caller owns it)
+ * are queued on the handle's stream, and *S is valid once that stream has been
+ * synchronised.  For a pipeline that reads every step's result without
+ * stalling the next step's upload.  No finiteness check (the caller sees the
+ * value); PF_EINVAL for a null handle or output, PF_ECUDA on a launch error. */
+int pf_solute_total_async(pf_handle* h, double* S);
+
 /* Front diagnostics: x_front = largest phi = 0.5 crossing along x over all
  * rows (linear interpolation, lab frame including window shifts; NaN when no
  * row has a crossing); v_front = (x_front - previous x_front)/(t - previous t)

@@ -555,6 +555,17 @@ int pf_solute_total(pf_handle* h, double* S) {
     return PF_OK;
 }
 
+int pf_solute_total_async(pf_handle* h, double* S) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!S) return fail(h, PF_EINVAL, "null output");
+    cudaError_t e = pf::launch_energy_solute(h->P, h->buf[h->cur], h->step, h->shifts, false, h->scratch,
+                                             h->dres, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S, h->dres + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "solute total");
+    return PF_OK;
+}
+
 int pf_front(pf_handle* h, double* x_front, double* v_front, double* c_max) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!x_front || !v_front || !c_max) return fail(h, PF_EINVAL, "null output");

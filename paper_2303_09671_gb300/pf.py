@@ -93,6 +93,7 @@ _SIGS = {
     "pf_set_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "pf_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "pf_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "pf_solute_total_async": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pf_set_fields_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int64]),
     "pf_energy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pf_step_energies": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
@@ -249,6 +250,14 @@ class Sim:
         v = ctypes.c_double()
         _check(lib().pf_solute_total(self._h, ctypes.byref(v)), self._h)
         return v.value
+
+    def solute_total_async(self, out, i: int = 0):
+        """Queue S_h into out[i] (a float64 numpy array, page-locked for the copy
+        to be asynchronous); valid after the handle's stream is synchronised."""
+        if out.dtype != np.float64 or not out.flags.c_contiguous or not 0 <= i < out.size:
+            raise ValueError("out must be a contiguous float64 array and i an index into it")
+        ptr = ctypes.cast(out.ctypes.data + 8 * int(i), ctypes.POINTER(ctypes.c_double))
+        _check(lib().pf_solute_total_async(self._h, ptr), self._h)
 
     def front(self):
         x, v, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -422,6 +422,29 @@ def test_set_fields_step_back_to_back(precision):
         assert all(np.array_equal(a, b) for a, b in zip(want[0], got))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_solute_total_async_pipeline(precision):
+    """Overlapped uploads each followed by a queued (not awaited) solute read
+    into page-locked memory: after one stream wait every entry equals the
+    synchronous pf_solute_total of the same state, bit for bit."""
+    torch = pytest.importorskip("torch")
+    dt = np.float64 if precision == "fp64" else np.float32
+    pr, phi, cs, cl = wl.random_state(3, (48, 19, 70), dx=0.5, A=1.5, b=0.3, a=-0.3, seed=33)
+    host = [torch.from_numpy(np.ascontiguousarray(x, dtype=dt)).pin_memory().numpy() for x in (phi, cs, cl)]
+    with Sim(pr, precision) as s:
+        s.set_fields_step(*host, n=1)
+        want = s.solute_total()
+    out = torch.zeros(4, dtype=torch.float64).pin_memory().numpy()
+    with Sim(pr, precision) as s:
+        for i in range(4):
+            s.set_clock(0, 0)
+            s.set_fields_step(*host, n=1)
+            s.solute_total_async(out, i)
+        torch.cuda.synchronize()
+        s.solute_total()   # synchronises the handle's stream as well
+    assert np.array_equal(out, np.full(4, want))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", ["planar1d", "pulled1d", "random3d"])
 def test_step_energies_match_per_call_energies(precision, case):
