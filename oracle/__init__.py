@@ -41,6 +41,15 @@ PLANT = {
     "mu_s_cryst": 64,
 }
 
+# planted mistakes of the front locator and the moving window (tests only); the
+# rates do not see them, so they are pinned separately from PLANT
+PLANT_WINDOW = {
+    "front_index": 128,
+    "front_half": 256,
+    "fresh_cinf": 512,
+    "shift_early": 1024,
+}
+
 
 class _Params(ctypes.Structure):
     _fields_ = [
@@ -141,7 +150,7 @@ def _params(p: dict) -> _Params:
     s.form = {"cd": 0, "literal": 1}[p.get("form", "cd")]
     plant = p.get("plant", 0)
     if isinstance(plant, str):
-        plant = PLANT[plant]
+        plant = PLANT[plant] if plant in PLANT else PLANT_WINDOW[plant]
     s.plant = int(plant)
     return s
 

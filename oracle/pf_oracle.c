@@ -30,6 +30,11 @@
 #define PLANT_TANG_SIGN     16   /* wrong sign of the tangential projection */
 #define PLANT_SWAP_W        32   /* swap the solid/liquid anti-trapping weights */
 #define PLANT_MU_S_CRYST    64   /* crystallisation force with mu_s instead of mu_l */
+/* planted mistakes of the diagnostics and the moving window (tests only) */
+#define PLANT_FRONT_INDEX  128   /* phi = 0.5 crossing placed one cell too low */
+#define PLANT_FRONT_HALF   256   /* crossing measured from the cell edge, not its centre */
+#define PLANT_FRESH_CINF   512   /* fresh hot-end layer with c_s = c_inf instead of the Dirichlet c_s */
+#define PLANT_SHIFT_EARLY 1024   /* window shifted once v t exceeds shifts dx (one shift ahead) */
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -561,7 +566,12 @@ int orc_front(const orc_params* P, const orc_clock* clk, const double* phi,
             for (int64_t i = L.n[0] - 2; i >= 0; --i) {
                 double a = phi[uidx(&L, i, j, k)], b = phi[uidx(&L, i + 1, j, k)];
                 if (a >= 0.5 && b < 0.5) {
-                    double x = ((double)i + 0.5 + (a - 0.5) / (a - b)) * P->dx +
+                    /* linear interpolation between the centres (i + 1/2) dx
+                     * and (i + 3/2) dx of the two cells, in the lab frame */
+                    double centre = (double)i + 0.5;
+                    if (P->plant & PLANT_FRONT_INDEX) centre -= 1.0;
+                    if (P->plant & PLANT_FRONT_HALF) centre -= 0.5;
+                    double x = (centre + (a - 0.5) / (a - b)) * P->dx +
                                (double)clk->shifts * P->dx;
                     if (x > xf) xf = x;
                     break;
@@ -622,13 +632,17 @@ int orc_step(const orc_params* P, orc_clock* clk, double* phi, double* cs,
         clk->step += 1;
         if (P->shift) {
             double t = (double)clk->step * P->dt;
-            while (P->v_pull * t >= (double)(clk->shifts + 1) * P->dx) {
+            /* the window has moved shifts cells when v_pull t first reaches
+             * shifts dx (Sec. "Numerical technique") */
+            const int64_t ahead = (P->plant & PLANT_SHIFT_EARLY) ? 0 : 1;
+            while (P->v_pull * t >= (double)(clk->shifts + ahead) * P->dx) {
                 /* cut the cold-end layer, add a fresh hot-end layer */
                 int64_t n = L->n[0];
                 memmove(phi, phi + 1, (n - 1) * sizeof(double));
                 memmove(cs, cs + 1, (n - 1) * sizeof(double));
                 memmove(cl, cl + 1, (n - 1) * sizeof(double));
                 phi[n - 1] = P->dir_phi; cs[n - 1] = P->dir_cs; cl[n - 1] = P->dir_cl;
+                if (P->plant & PLANT_FRESH_CINF) cs[n - 1] = P->c_inf;
                 clk->shifts += 1;
             }
         }

@@ -1,0 +1,235 @@
+"""Pins of the oracle's front locator (orc_front) and of its moving window (the
+shift inside orc_step), against what the mathematics and the paper fix.
+
+No GPU.  The front locator takes the largest phi = 1/2 crossing along x by
+linear interpolation between cell centres; the window (Sec. "Numerical
+technique") drops the cold-end cell and appends a fresh hot-end cell held at
+the Dirichlet state whenever the pulling distance v t reaches the next
+multiple of dx.  Each planted mistake of oracle.PLANT_WINDOW fails at least
+one of these pins.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09671_gb300 import workloads as wl
+
+SQ2 = math.sqrt(2.0)
+
+
+def profile_params(n, dx, dim=1, **kw):
+    return wl.scaled_params(dim, n, dx, 0.1, 2.0, 0.1, A=1.0, b=1.0, dt=1e-3, **kw)
+
+
+def tanh_row(n, dx, x_f):
+    """phi_0 = (1 - tanh((x - x_f)/(sqrt 2 W)))/2 at the cell centres
+    (supplement Eq. eq18, W = 1), solid at low x."""
+    x = (np.arange(n) + 0.5) * dx
+    return 0.5 * (1.0 - np.tanh((x - x_f) / SQ2))
+
+
+def front_of(pr, phi, cs=None, cl=None, shifts=0):
+    cs = np.full_like(phi, 0.1) if cs is None else cs
+    cl = np.ones_like(phi) if cl is None else cl
+    st = oracle.State(pr, phi, cs, cl, shifts=shifts)
+    return st.front()
+
+
+# ------------------------------------------------------------------ front locator
+
+@pytest.mark.parametrize("dx", [0.25, 0.5, 0.8])
+@pytest.mark.parametrize("i_face,shifts", [(40, 0), (57, 0), (40, 13)])
+def test_front_exact_when_the_profile_is_centred_on_a_cell_face(dx, i_face, shifts):
+    """Centred on the face between cells i-1 and i, the odd profile gives
+    phi_{i-1} - 1/2 = 1/2 - phi_i, so linear interpolation between the two cell
+    centres lands on the face itself: x_front = i dx (+ shifts dx in the lab
+    frame) to rounding, at any dx."""
+    n = 128
+    pr = profile_params((n,), dx)
+    phi = tanh_row(n, dx, i_face * dx)
+    xf, _ = front_of(pr, phi, shifts=shifts)
+    assert abs(xf - (i_face + shifts) * dx) <= 1e-13 * (i_face + shifts) * dx
+
+
+def test_front_exact_when_the_profile_is_centred_on_a_cell():
+    """phi = 1/2 exactly at a cell centre: x_front is that centre."""
+    n, dx = 100, 0.5
+    pr = profile_params((n,), dx)
+    phi = tanh_row(n, dx, 30.5 * dx)
+    phi[30] = 0.5
+    xf, _ = front_of(pr, phi)
+    assert xf == 30.5 * dx
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.35, 0.8])
+def test_front_off_face_error_is_the_third_order_interpolation_term(alpha):
+    """Front at fraction alpha of the way from a cell centre to the next:
+    for g = phi_0 - 1/2 = -s/(2 sqrt 2) + s^3/(12 sqrt 2) + O(s^5) (s = x - x_f),
+    the root of the chord through (x_f + u1, x_f + u2), u1 = -alpha dx,
+    u2 = (1 - alpha) dx, lies at x_f + (b/a) u1 u2 (u1 + u2) + O(dx^5) with
+    b/a = -1/6, i.e. x_f + alpha (1 - alpha)(1 - 2 alpha) dx^3 / 6.  Checked
+    against that term, and halving dx divides the error by ~8."""
+    n = 400
+    errs = []
+    for dx in (0.4, 0.2, 0.1):
+        pr = profile_params((n,), dx)
+        c = 150
+        x_f = (c + 0.5 + alpha) * dx
+        xf, _ = front_of(pr, tanh_row(n, dx, x_f))
+        err = xf - x_f
+        lead = alpha * (1 - alpha) * (1 - 2 * alpha) * dx ** 3 / 6.0
+        assert abs(err - lead) <= 0.05 * dx ** 5 + 1e-14, (dx, err, lead)
+        errs.append(err)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 7.0 < r1 < 9.0 and 7.5 < r2 < 8.5, (r1, r2)
+
+
+def test_front_takes_the_largest_crossing_over_rows_and_within_a_row():
+    """2D: the largest crossing over all rows; a row with two solid-liquid
+    crossings contributes its larger one; a row that is all liquid contributes
+    none.  With no crossing anywhere x_front is NaN."""
+    nx, ny, dx = 120, 4, 0.5
+    pr = profile_params((nx, ny), dx, dim=2)
+    phi = np.zeros((ny, nx))
+    phi[0] = tanh_row(nx, dx, 20.0 * dx)
+    # row 1: solid, liquid, solid, liquid (crossings near 10 and 50 cells)
+    phi[1] = np.maximum(tanh_row(nx, dx, 10.0 * dx),
+                        np.minimum(1 - tanh_row(nx, dx, 30.0 * dx), tanh_row(nx, dx, 50.0 * dx)))
+    phi[2] = tanh_row(nx, dx, 35.0 * dx)
+    # row 3 all liquid
+    xf, _ = front_of(pr, phi)
+    assert abs(xf - 50.0 * dx) <= 1e-3
+    xf0, _ = front_of(pr, np.zeros((ny, nx)))
+    assert np.isnan(xf0)
+
+
+def test_cmax_on_constructed_states():
+    """c_max is the largest mixture concentration c = p c_s + (1-p) c_l
+    (Eq. model1 with g = p): where phi = 0 it is c_l (p(0) = 0), where phi = 1
+    it is c_s (p(1) = 1), and at phi = 1/2 the mean of the two (p(1/2) = 1/2 by
+    the antisymmetry of p), exactly."""
+    n, dx = 64, 0.5
+    pr = profile_params((n,), dx)
+    phi = np.zeros(n)
+    cs, cl = np.full(n, 0.1), np.ones(n)
+    cl[17] = 1.7
+    assert front_of(pr, phi, cs, cl)[1] == 1.7
+    phi[:] = 1.0
+    cs[41] = 2.3
+    assert front_of(pr, phi, cs, cl)[1] == 2.3
+    phi[:] = 0.0
+    phi[5] = 0.5
+    cs[5], cl[5] = 3.0, 2.0
+    assert front_of(pr, phi, cs, cl)[1] == 2.5
+
+
+@pytest.mark.parametrize("plant", ["front_index", "front_half"])
+def test_planted_front_mistakes_fail_the_face_pin(plant):
+    n, dx = 128, 0.5
+    pr = dict(profile_params((n,), dx), plant=plant)
+    xf, _ = front_of(pr, tanh_row(n, dx, 40 * dx))
+    assert abs(xf - 40 * dx) >= 0.25 * dx
+
+
+# ------------------------------------------------------------------ moving window
+
+def pulled(N=256, V=0.37, **kw):
+    pr, phi, cs, cl = wl.pulled_front_1d(N=N, dx=0.5, V=V, k_e=0.1, D_s=0.1, A=1.0, b=1.0,
+                                         G_theta=0.2, front_cell=64, **kw)
+    pr["dt"] = min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / V)
+    return pr, phi, cs, cl
+
+
+def run_window_checks(pr, phi, cs, cl, nsteps):
+    """Step one at a time; after every step check the shift count against
+    floor(v t / dx), and after every step that shifted, the fresh layer and the
+    move of the rest of the state against an unshifted copy of the same step."""
+    st = oracle.State(pr, phi, cs, cl)
+    no_shift = dict(pr, shift=False)
+    seen = 0
+    for _ in range(nsteps):
+        ref = oracle.State(no_shift, st.phi, st.cs, st.cl, step=st.clock.step, shifts=st.clock.shifts)
+        ref.step(1)
+        before = st.clock.shifts
+        st.step(1)
+        t = st.clock.step * pr["dt"]
+        assert st.clock.shifts == math.floor(pr["v_pull"] * t / pr["dx"]), (st.clock.step, st.clock.shifts)
+        k = st.clock.shifts - before
+        if k == 0:
+            assert np.array_equal(st.phi, ref.phi) and np.array_equal(st.cs, ref.cs)
+            continue
+        seen += 1
+        assert k == 1
+        # the rest of the state moves down by one cell ...
+        for a, b in ((st.phi, ref.phi), (st.cs, ref.cs), (st.cl, ref.cl)):
+            assert np.array_equal(a[:-1], b[1:])
+        # ... and the fresh hot-end cell is the Dirichlet state (phi = 0,
+        # c_s = k_e c_inf, c_l = c_inf), the values the hot end is held at
+        dphi, dcs, dcl = pr["dirichlet"]
+        assert (st.phi[-1], st.cs[-1], st.cl[-1]) == (dphi, dcs, dcl)
+        assert dcs == pr["k_e"] * pr["c_inf"] and dcl == pr["c_inf"]
+    return st, seen
+
+
+def test_window_shift_count_fresh_layer_and_move():
+    pr, phi, cs, cl = pulled()
+    st, seen = run_window_checks(pr, phi, cs, cl, 400)
+    assert seen >= 20
+
+
+def test_temperature_is_continuous_across_a_shift():
+    """theta(x, t) = theta_ref - G ((x - x0) - v t) is a function of the lab
+    position (Eq. ds1): the rates of a state whose window moved by one cell
+    (fields moved down, clock shifts + 1) equal those of the unmoved state one
+    cell higher, away from the hot end."""
+    pr, phi, cs, cl = pulled(N=200)
+    st = oracle.State(pr, phi, cs, cl, step=37, shifts=0)
+    st.step(50)
+    r0 = st.rates()
+    mv = [np.concatenate([a[1:], [v]]) for a, v in zip((st.phi, st.cs, st.cl), pr["dirichlet"])]
+    sh = oracle.State(pr, *mv, step=st.clock.step, shifts=st.clock.shifts + 1)
+    r1 = sh.rates()
+    for a, b in zip(r1, r0):
+        # cells whose two-cell neighbourhood is the same in both (not the ends)
+        assert np.allclose(a[2:-3], b[3:-2], rtol=1e-13, atol=1e-13 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("plant", ["fresh_cinf", "shift_early"])
+def test_planted_window_mistakes_fail_the_window_pins(plant):
+    pr, phi, cs, cl = pulled()
+    with pytest.raises(AssertionError):
+        run_window_checks(dict(pr, plant=plant), phi, cs, cl, 400)
+
+
+def test_pulled_front_reaches_steady_state_by_mass_balance():
+    """Check (d) on the oracle itself: a pulled front (k_e = 0.1, D_s/D_l = 0.1,
+    A = b = 1, frozen gradient 0.2 per W, V = 0.5) run in the moving window to
+    steady state.  In the frame of the window the front stands still and the
+    solid it leaves behind carries the alloy composition c_inf (Eq. model5:
+    the solute that enters at the hot end leaves through the solid), so the
+    mixture concentration 10-20 W behind the front is c_inf; the partition
+    coefficient k_v = c_inf / c_max has settled between k_e and 1, and the
+    front advances exactly with the window."""
+    pr, phi, cs, cl = pulled(N=1024, V=0.5)
+    st = oracle.State(pr, phi, cs, cl)
+    st.step(8000)
+    x1, c1 = st.front()
+    s1 = st.clock.shifts
+    st.step(2000)
+    x2, c2 = st.front()
+    f = st.phi
+    j = np.where((f[:-1] >= 0.5) & (f[1:] < 0.5))[0]
+    assert len(j) == 1 and 64 < j[0] < 200
+    # steady: the front moves with the window, v_front = v_pull
+    v_front = (x2 - x1) / (2000 * pr["dt"])
+    assert abs(v_front - pr["v_pull"]) <= 1e-9 * pr["v_pull"], v_front
+    assert st.clock.shifts - s1 == round(2000 * pr["dt"] * pr["v_pull"] / pr["dx"])
+    assert abs(c2 - c1) <= 1e-7 * c1      # |dk/dt| below 1e-9 per unit time
+    p = f ** 3 * (6 * f * f - 15 * f + 10)
+    c = p * st.cs + (1 - p) * st.cl
+    behind = c[j[0] - 40:j[0] - 20]
+    assert np.abs(behind - pr["c_inf"]).max() <= 1e-3 * pr["c_inf"], behind
+    k = pr["c_inf"] / c2
+    assert pr["k_e"] < k < 1.0
