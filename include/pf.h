@@ -338,19 +338,26 @@ int pf_adjoint(const pf_adjoint_desc* desc, pf_adjoint_result* res, void* stream
  * monitoring or real-time path that must not block or fail on cudaMalloc, or a
  * caller without a pf_handle, since pf_create allocates).
  *
- * Computes the same F_h (out[0]) and S_h (out[1]) as pf_energy and
- * pf_solute_total, directly from caller-owned device arrays phi, cs, cl of
- * n[0]*n[1]*n[2] values (x fastest, element type of params->precision) at the
- * clock (step, shifts), and writes the two doubles to the caller-owned device
- * pointer `out`, ordered on `stream` (no host synchronisation).  It calls no
- * cudaMalloc/cudaFree: the reduction's block partials live in a 19 KiB
- * file-scope device array that stays resident on every GPU that loads the
- * library.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) and must therefore come before any stream capture
- * on that device.  All calls share the array; each call rewrites every partial
- * it reads, but calls whose kernels overlap on the GPU race and must be
- * serialised by the caller.  Grids above 2^30 cells, invalid sizes or
- * parameters return PF_EINVAL (message via pf_last_error(NULL)). */
+ * Computes F_h (out[0]) and S_h (out[1]) as pf_energy and pf_solute_total do
+ * (the same reduction kernel and grid), directly from caller-owned device
+ * arrays phi, cs, cl of n[0]*n[1]*n[2] values (x fastest, element type of
+ * params->precision: float for PF_FP32, double for PF_FP64) at the clock
+ * (step, shifts), and writes the two doubles to the caller-owned device
+ * pointer `out` (at least 2 doubles), ordered on `stream` (no host
+ * synchronisation).  It calls no cudaMalloc/cudaFree: the reduction's block
+ * partials live in a 32 KiB file-scope device array that stays resident on
+ * every GPU that loads the library.  Every call looks the array's device
+ * address up (cudaGetSymbolAddress, no allocation); the first call on a
+ * device also loads the library's device code there, so make it before any
+ * stream capture on that device.  All calls share the array; each call
+ * rewrites every partial it reads, but calls whose kernels overlap on the GPU
+ * race and must be serialised by the caller.  Returns PF_EINVAL (message via
+ * pf_last_error(NULL)) for null pointers, a negative clock, grids above 2^30
+ * cells, and every description pf_create rejects except for the conditions
+ * that concern stepping only (dt above the stability bound, the moving
+ * window, the 2D/3D step-launch limits); dt must be finite.  The pointers
+ * themselves cannot be checked here: they must address device memory of the
+ * sizes above. */
 int pf_energy_solute_noalloc(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
                              int64_t step, int64_t shifts, const void* phi, const void* cs,
                              const void* cl, double* out, void* stream);

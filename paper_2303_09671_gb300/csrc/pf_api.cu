@@ -89,7 +89,11 @@ double stable_dt(const pf_grid* g, const pf_params* p) {
     return std::fmin(dt_phi, dt_c);
 }
 
-std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
+}  // namespace
+
+namespace pf {
+
+std::string validate_problem(const pf_grid* g, const pf_bc* bc, const pf_params* p, bool stepping) {
     if (!g || !bc || !p) return "null argument";
     if (g->dim < 1 || g->dim > 3) return "dim must be 1, 2 or 3";
     for (int a = 0; a < 3; ++a) {
@@ -108,9 +112,10 @@ std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
         return "grid too large";
     // launch limits of the 2D/3D kernels: one CTA row per 8 or 16 cells of y in
     // grid.y (at most 65535), and 32-bit offsets within an x-y plane
-    if (g->dim >= 2 && g->n[1] > int64_t(65535) * 8) return "n[1] above 524280 is not supported";
-    if (g->dim == 3 && g->n[0] * g->n[1] > int64_t(0x7fffffff)) return "an x-y plane above 2^31 - 1 cells is not supported";
-    if (!(g->dx > 0)) return "dx must be positive";
+    if (stepping && g->dim >= 2 && g->n[1] > int64_t(65535) * 8) return "n[1] above 524280 is not supported";
+    if (stepping && g->dim == 3 && g->n[0] * g->n[1] > int64_t(0x7fffffff))
+        return "an x-y plane above 2^31 - 1 cells is not supported";
+    if (!(g->dx > 0) || !std::isfinite(g->dx)) return "dx must be positive and finite";
     if (p->precision != PF_FP32 && p->precision != PF_FP64) return "precision must be PF_FP32 or PF_FP64";
     if (p->interp != PF_INTERP_QUINTIC && p->interp != PF_INTERP_CUBIC) return "unknown interp";
     if (p->mobility_mode != PF_MOBILITY_DC && p->mobility_mode != PF_MOBILITY_CONST)
@@ -125,9 +130,13 @@ std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
     if (!(p->b > 0)) return "b must be positive";
     if (!(p->delta >= 0)) return "delta must be non-negative";
     if (!(p->c_inf > 0)) return "c_inf must be positive";
-    if (!std::isfinite(p->A) || !std::isfinite(p->a) || !std::isfinite(p->theta_ref) ||
-        !std::isfinite(p->G_theta) || !std::isfinite(p->v_pull) || !std::isfinite(p->x0))
+    if (!std::isfinite(p->H) || !std::isfinite(p->sigma) || !std::isfinite(p->M_phi) || !std::isfinite(p->D_s) ||
+        !std::isfinite(p->D_l) || !std::isfinite(p->b) || !std::isfinite(p->delta) || !std::isfinite(p->c_inf) ||
+        !std::isfinite(p->A) || !std::isfinite(p->a) || !std::isfinite(p->theta_ref) ||
+        !std::isfinite(p->G_theta) || !std::isfinite(p->v_pull) || !std::isfinite(p->x0) ||
+        !std::isfinite(bc->dir_phi) || !std::isfinite(bc->dir_cs) || !std::isfinite(bc->dir_cl))
         return "non-finite parameter";
+    if (!stepping) return std::isfinite(p->dt) ? "" : "non-finite parameter";
     if (p->shift && g->dim != 1) return "the moving window is supported in 1D only";
     if (p->shift && !(p->v_pull * p->dt < g->dx)) return "v_pull dt must be below dx";
     if (!(p->dt > 0)) return "dt must be positive";
@@ -136,7 +145,28 @@ std::string validate(const pf_grid* g, const pf_bc* bc, const pf_params* p) {
     return "";
 }
 
-}  // namespace
+void fill_problem(HostProblem& P, const pf_grid* grid, const pf_bc* bc, const pf_params* params) {
+    P.dim = grid->dim;
+    for (int a = 0; a < 3; ++a) {
+        P.n[a] = (a < grid->dim) ? grid->n[a] : 1;
+        P.bc_lo[a] = (a < grid->dim) ? bc->lo[a] : PF_BC_NOFLUX;
+        P.bc_hi[a] = (a < grid->dim) ? bc->hi[a] : PF_BC_NOFLUX;
+    }
+    P.dx = grid->dx;
+    P.dir_phi = bc->dir_phi; P.dir_cs = bc->dir_cs; P.dir_cl = bc->dir_cl;
+    P.precision = params->precision;
+    P.interp = params->interp;
+    P.lap = params->lap_stencil;
+    P.mobility = params->mobility_mode;
+    P.H = params->H; P.sigma = params->sigma; P.M_phi = params->M_phi;
+    P.D_s = params->D_s; P.D_l = params->D_l; P.k_e = params->k_e;
+    P.A = params->A; P.b = params->b; P.a = params->a; P.delta = params->delta;
+    P.theta_ref = params->theta_ref; P.G_theta = params->G_theta;
+    P.v_pull = params->v_pull; P.x0 = params->x0; P.dt = params->dt; P.c_inf = params->c_inf;
+    P.shift = params->shift ? 1 : 0;
+}
+
+}  // namespace pf
 
 namespace pf {
 // message returned by pf_last_error(NULL) (failed pf_create / pf_run_batch)
@@ -162,29 +192,12 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
               pf_handle** out) {
     if (!out) return fail(nullptr, PF_EINVAL, "null output pointer");
     *out = nullptr;
-    const std::string why = validate(grid, bc, params);
+    const std::string why = pf::validate_problem(grid, bc, params, true);
     if (!why.empty()) return fail(nullptr, PF_EINVAL, why);
     pf_handle* h = new (std::nothrow) pf_handle();
     if (!h) return fail(nullptr, PF_ENOMEM, "host allocation failed");
     pf::HostProblem& P = h->P;
-    P.dim = grid->dim;
-    for (int a = 0; a < 3; ++a) {
-        P.n[a] = grid->n[a];
-        P.bc_lo[a] = (a < grid->dim) ? bc->lo[a] : PF_BC_NOFLUX;
-        P.bc_hi[a] = (a < grid->dim) ? bc->hi[a] : PF_BC_NOFLUX;
-    }
-    P.dx = grid->dx;
-    P.dir_phi = bc->dir_phi; P.dir_cs = bc->dir_cs; P.dir_cl = bc->dir_cl;
-    P.precision = params->precision;
-    P.interp = params->interp;
-    P.lap = params->lap_stencil;
-    P.mobility = params->mobility_mode;
-    P.H = params->H; P.sigma = params->sigma; P.M_phi = params->M_phi;
-    P.D_s = params->D_s; P.D_l = params->D_l; P.k_e = params->k_e;
-    P.A = params->A; P.b = params->b; P.a = params->a; P.delta = params->delta;
-    P.theta_ref = params->theta_ref; P.G_theta = params->G_theta;
-    P.v_pull = params->v_pull; P.x0 = params->x0; P.dt = params->dt; P.c_inf = params->c_inf;
-    P.shift = params->shift ? 1 : 0;
+    pf::fill_problem(P, grid, bc, params);
     h->stream = static_cast<cudaStream_t>(stream);
     if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
     if (const char* oc = std::getenv("PF_OVCHUNK")) h->ovchunk = std::atoi(oc);

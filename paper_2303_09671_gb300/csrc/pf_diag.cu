@@ -2,10 +2,12 @@
 // c_max), the 1D moving-window shift and the conversions between the
 // caller's (phi, c_s, c_l) and the device state (phi, c, d[, c_lo]).
 //
-// Reductions are deterministic: a grid fixed by the problem size (at most
-// DIAG_BLOCKS blocks, fewer for small grids, so that a 1D run does not launch
-// a thousand idle blocks every step) writes one partial per block (warp-shuffle
-// tree inside the block), and a single block sums the partials in a fixed order.
+// Reductions are deterministic: a grid fixed by the problem size and the
+// device (at most 8 blocks per SM, fewer for small grids, so that a 1D run does
+// not launch a thousand idle blocks every step) writes one partial per block
+// (warp-shuffle tree inside the block), and a single block sums the partials in
+// a fixed order.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include "pf_internal.cuh"
@@ -14,15 +16,39 @@
 namespace pf {
 
 static constexpr int DIAG_THREADS = 256;
-static constexpr int DIAG_BLOCKS = 1216;   // 8 per SM on a 152-SM GB300
 
-size_t diag_scratch_doubles(const HostProblem&) { return 2 * (size_t)DIAG_BLOCKS; }
+size_t diag_scratch_doubles(const HostProblem&) { return 2 * (size_t)DIAG_MAX_BLOCKS; }
 
-// blocks for a grid-stride pass over `items`: one per 64 items up to DIAG_BLOCKS,
-// so that small FP64 problems spread their (slow) FP64 work over many SMs
+// largest grid of the reductions and conversions on the current device: 8
+// blocks of 256 threads per SM (the SM count queried once per device), at most
+// DIAG_MAX_BLOCKS
+static int diag_grid() {
+    static DeviceSetup setup;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= DeviceSetup::MAX_DEVICES) {
+        cudaGetLastError();
+        return DIAG_MAX_BLOCKS;
+    }
+    std::lock_guard<std::mutex> lock(setup.mu);
+    if (!setup.done[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = DIAG_MAX_BLOCKS / 8;
+        }
+        setup.value[dev] = (size_t)std::min(8 * sms, DIAG_MAX_BLOCKS);
+        setup.done[dev] = true;
+    }
+    return (int)setup.value[dev];
+}
+
+// blocks for a grid-stride pass over `items`: one per 64 items up to
+// diag_grid(), so that small FP64 problems spread their (slow) FP64 work over
+// many SMs
 static int diag_blocks(long long items) {
     const long long b = (items + 63) / 64;
-    return (int)(b < 1 ? 1 : (b > DIAG_BLOCKS ? DIAG_BLOCKS : b));
+    const long long cap = diag_grid();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 struct DiagConsts {
@@ -81,25 +107,52 @@ struct StateView {
     __device__ __forceinline__ double cval(long long i) const {
         return (double)c[i] + (clo ? (double)clo[i] : 0.0);
     }
+    // total c, and (ENERGY) phi, p(phi), c_s, c_l of cell i
+    template <bool ENERGY>
+    __device__ __forceinline__ void cell(const DiagConsts& C, long long i, double& cc, double& f, double& p,
+                                         double& s, double& l) const {
+        cc = cval(i);
+        if (!ENERGY) return;
+        f = (double)phi[i];
+        const double dd = (double)d[i];
+        p = p_d(C, f);
+        s = cc + (1.0 - p) * dd;
+        l = cc - p * dd;
+    }
 };
 
-template <typename T, bool ENERGY>
+// the caller's fields (phi, c_s, c_l) read directly (pf_energy_solute_noalloc)
+template <typename T>
+struct FieldView {
+    const T* phi;
+    const T* cs;
+    const T* cl;
+    template <bool ENERGY>
+    __device__ __forceinline__ void cell(const DiagConsts& C, long long i, double& cc, double& f, double& p,
+                                         double& s, double& l) const {
+        f = (double)phi[i];
+        s = (double)cs[i];
+        l = (double)cl[i];
+        p = p_d(C, f);
+        cc = p * s + (1.0 - p) * l;   // Eq. model1 with g = p
+    }
+};
+
+template <typename View, bool ENERGY>
 __global__ void __launch_bounds__(DIAG_THREADS)
-energy_solute_kernel(StateView<T> S, DiagConsts C, double* __restrict__ part) {
+energy_solute_kernel(View S, DiagConsts C, double* __restrict__ part) {
     const long long N = (long long)C.n[0] * C.n[1] * C.n[2];
     double eF = 0.0, eS = 0.0;
     const double one_m_ke = 1.0 - C.k_e, log_ke = log(C.k_e);
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
-        const double cc = S.cval(c);
+        double cc, f = 0.0, p = 0.0, s = 0.0, l = 0.0;
+        S.template cell<ENERGY>(C, c, cc, f, p, s, l);
         eS += cc;
         if (!ENERGY) continue;
         const int i = (int)(c % C.n[0]);
         const int j = (int)((c / C.n[0]) % C.n[1]);
         const int k = (int)(c / ((long long)C.n[0] * C.n[1]));
-        const double f = (double)S.phi[c], d = (double)S.d[c];
-        const double p = p_d(C, f);
-        const double s = cc + (1.0 - p) * d, l = cc - p * d;
         const double theta = C.theta0 - C.G_theta * (((double)i + 0.5) * C.dx);
         const double fs = -one_m_ke * theta + s * (log(s) - log_ke - 1.0);
         const double fl = l * (log(l) - 1.0);
@@ -410,14 +463,32 @@ cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t 
     const DiagConsts C = make_diag(P, step, shifts);
     const int nb = diag_blocks(P.cells());
     if (P.precision == 1) {
-        if (with_energy) energy_solute_kernel<double, true><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
-        else energy_solute_kernel<double, false><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+        if (with_energy)
+            energy_solute_kernel<StateView<double>, true><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
+        else
+            energy_solute_kernel<StateView<double>, false><<<nb, DIAG_THREADS, 0, s>>>(view<double>(f), C, scratch);
     } else {
-        if (with_energy) energy_solute_kernel<float, true><<<nb, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
+        if (with_energy)
+            energy_solute_kernel<StateView<float>, true><<<nb, DIAG_THREADS, 0, s>>>(view<float>(f), C, scratch);
         else solute_f32_kernel<<<nb, DIAG_THREADS, 0, s>>>(
             (const float*)f.c, (const float*)f.clo, P.cells(), scratch);
     }
     finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, nb, C.dV, out, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_solute_fields(const HostProblem& P, const void* phi, const void* cs, const void* cl,
+                                        int64_t step, int64_t shifts, double* scratch, double* out,
+                                        cudaStream_t s) {
+    const DiagConsts C = make_diag(P, step, shifts);
+    const int nb = diag_blocks(P.cells());
+    if (P.precision == 1)
+        energy_solute_kernel<FieldView<double>, true><<<nb, DIAG_THREADS, 0, s>>>(
+            FieldView<double>{(const double*)phi, (const double*)cs, (const double*)cl}, C, scratch);
+    else
+        energy_solute_kernel<FieldView<float>, true><<<nb, DIAG_THREADS, 0, s>>>(
+            FieldView<float>{(const float*)phi, (const float*)cs, (const float*)cl}, C, scratch);
+    finish_sum2<<<1, DIAG_THREADS, 0, s>>>(scratch, nb, C.dV, out, nullptr);
     return cudaGetLastError();
 }
 
@@ -460,12 +531,12 @@ cudaError_t launch_to_state(const HostProblem& P, const void* phi, const void* c
     const DiagConsts C = make_diag(P, 0, 0);
     const long long n = P.cells();
     if (P.precision == 1)
-        to_state_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+        to_state_kernel<double><<<diag_grid(), DIAG_THREADS, 0, s>>>(
             (const double*)phi, (const double*)cs, (const double*)cl, n, C, (double*)out.phi,
             (double*)out.c, (double*)out.d, nullptr);
     else
         to_state_f32((const float*)phi, (const float*)cs, (const float*)cl, n, C, (float*)out.phi,
-                     (float*)out.c, (float*)out.d, (float*)out.clo, (float*)out.plo, DIAG_BLOCKS, s);
+                     (float*)out.c, (float*)out.d, (float*)out.clo, (float*)out.plo, diag_grid(), s);
     return cudaGetLastError();
 }
 
@@ -474,7 +545,7 @@ cudaError_t launch_to_state_range(const HostProblem& P, const void* phi, const v
                                   cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const DiagConsts C = make_diag(P, 0, 0);
-    const int nb = blocks > 0 ? blocks : DIAG_BLOCKS;
+    const int nb = blocks > 0 ? blocks : diag_grid();
     if (P.precision == 1) {
         auto at = [&](const void* p) { return static_cast<const double*>(p) + first; };
         auto to = [&](void* p) { return static_cast<double*>(p) + first; };
@@ -494,10 +565,10 @@ cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi,
     const DiagConsts C = make_diag(P, 0, 0);
     const long long n = P.cells();
     if (P.precision == 1)
-        from_state_kernel<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+        from_state_kernel<double><<<diag_grid(), DIAG_THREADS, 0, s>>>(
             view<double>(in), n, C, (double*)phi, (double*)cs, (double*)cl);
     else
-        from_state_kernel<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(
+        from_state_kernel<float><<<diag_grid(), DIAG_THREADS, 0, s>>>(
             view<float>(in), n, C, (float*)phi, (float*)cs, (float*)cl);
     return cudaGetLastError();
 }

@@ -6,6 +6,7 @@
 #include <mutex>
 #include <string>
 #include <cuda_runtime.h>
+#include "pf.h"
 
 namespace pf {
 
@@ -51,17 +52,25 @@ template <typename T>
 cudaError_t step3d_chunks(const HostProblem& P, int requested, int* zchunk, int* nchunks);
 size_t step_smem_bytes(int precision, int dim);
 
-// Diagnostics.  `scratch` must hold diag_scratch_doubles(prob) doubles; results
-// are written as doubles to out (device pointer):
+// Diagnostics.  `scratch` must hold diag_scratch_doubles(prob) doubles
+// (2 DIAG_MAX_BLOCKS: one partial pair per block of a reduction grid of at most
+// 8 blocks per SM and at most DIAG_MAX_BLOCKS blocks); results are written as
+// doubles to out (device pointer):
 //   energy_solute: out[0] = F_h, out[1] = S_h
 //   front:         out[0] = x_front (local, without the window offset; NaN if
 //                  none), out[1] = c_max
+constexpr int DIAG_MAX_BLOCKS = 2048;
 size_t diag_scratch_doubles(const HostProblem& P);
 cudaError_t launch_energy_solute(const HostProblem& P, const Fields& f, int64_t step,
                                  int64_t shifts, bool with_energy, double* scratch, double* out,
                                  cudaStream_t s, long long* slot = nullptr);
 cudaError_t launch_front(const HostProblem& P, const Fields& f, double* scratch, double* out,
                          cudaStream_t s);
+// energy_solute (with energy) from the caller's fields (phi, c_s, c_l) of P's
+// precision instead of a handle's state; same kernel, same reduction grid
+cudaError_t launch_energy_solute_fields(const HostProblem& P, const void* phi, const void* cs, const void* cl,
+                                        int64_t step, int64_t shifts, double* scratch, double* out,
+                                        cudaStream_t s);
 // moving window: out[i] = in[i+1] (i < n-1), out[n-1] = the Dirichlet state (1D)
 cudaError_t launch_shift(const HostProblem& P, const Fields& in, const Fields& out, cudaStream_t s);
 // (phi, c_s, c_l) of the caller's precision <-> the device state (phi, c, d[, c_lo])
@@ -89,5 +98,13 @@ struct DeviceSetup {
 
 cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
                               cudaStream_t s);
+
+// The checks of pf_create on a problem description (pf_api.cu): "" if valid,
+// else the reason.  stepping = false leaves out what only the time step needs
+// (the explicit stability bound on dt, the moving window, the launch limits of
+// the 2D/3D step kernels) and requires dt to be finite only.
+std::string validate_problem(const pf_grid* grid, const pf_bc* bc, const pf_params* params, bool stepping);
+// HostProblem from a validated description
+void fill_problem(HostProblem& P, const pf_grid* grid, const pf_bc* bc, const pf_params* params);
 
 }  // namespace pf

@@ -478,12 +478,46 @@ def kv_loss(theta, problem: KvProblem):
     return _KvLoss.apply(theta)
 
 
+def _noalloc_pointers(pr: dict, precision: str, phi, cs, cl, out):
+    """Device pointers of the arguments of pf_energy_solute_noalloc, after the
+    checks the C entry point cannot make on raw pointers: the three fields are
+    contiguous CUDA tensors of exactly prod(n) elements of the precision's
+    float type, and out a contiguous float64 CUDA tensor of at least 2 elements,
+    all on one device.  PFError(PF_EINVAL) otherwise, before anything runs."""
+    if precision not in PRECISION:
+        raise PFError(PF_EINVAL, f"unknown precision {precision!r}")
+    cells = 1
+    for v in list(pr["n"])[: int(pr["dim"])]:
+        cells *= int(v)
+    want = "torch.float64" if precision == "fp64" else "torch.float32"
+
+    def bad(msg):
+        return PFError(PF_EINVAL, "energy_solute_noalloc: " + msg)
+
+    for name, t in (("out", out), ("phi", phi), ("cs", cs), ("cl", cl)):
+        if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+            raise bad(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise bad(f"{name} must be contiguous")
+        if t.device != out.device:
+            raise bad(f"{name} is on {t.device}, out on {out.device}")
+    if str(out.dtype) != "torch.float64" or out.numel() < 2:
+        raise bad("out must be a float64 tensor of at least 2 elements")
+    for name, t in (("phi", phi), ("cs", cs), ("cl", cl)):
+        if str(t.dtype) != want:
+            raise bad(f"{name} has dtype {t.dtype}, the {precision} precision needs {want}")
+        if t.numel() != cells:
+            raise bad(f"{name} has {t.numel()} elements, the grid has {cells}")
+    return [_VP(t.data_ptr()) for t in (phi, cs, cl, out)]
+
+
 def energy_solute_noalloc(pr: dict, phi, cs, cl, out, precision="fp32", step=0, shifts=0, stream=None):
     """pf_energy_solute_noalloc on CUDA tensors: writes (F_h, S_h) into the
-    2-element float64 CUDA tensor `out` without allocating device memory."""
+    float64 CUDA tensor `out` (at least 2 elements) without allocating device
+    memory.  The fields are checked first (see _noalloc_pointers)."""
+    ptrs = _noalloc_pointers(pr, precision, phi, cs, cl, out)
     g, b, p = make_structs(pr, precision)
     s = _current_stream() if stream is None else stream
     rc = lib().pf_energy_solute_noalloc(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), int(step),
-                                        int(shifts), _VP(phi.data_ptr()), _VP(cs.data_ptr()),
-                                        _VP(cl.data_ptr()), _VP(out.data_ptr()), _VP(s))
+                                        int(shifts), *ptrs, _VP(s))
     _check(rc, None)

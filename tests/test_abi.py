@@ -127,3 +127,86 @@ def test_empty_batch_is_rejected_before_any_device_work():
         D.max_steps, D.steps_per_launch, D.launches_per_graph = 100, 10, 1
         R = pf.pf_batch_result()
         assert L.pf_run_batch(ctypes.byref(D), ctypes.byref(R), None) == pf.PF_EINVAL
+
+
+# ------------------------------------------------ pf_energy_solute_noalloc checks
+
+class _FakeCudaTensor:
+    """Stands in for a torch CUDA tensor in the argument checks of
+    pf.energy_solute_noalloc (no GPU here; nothing is dereferenced)."""
+
+    def __init__(self, numel, dtype="torch.float32", cuda=True, contiguous=True, device="cuda:0"):
+        self._n, self.dtype, self.is_cuda, self._c, self.device = numel, dtype, cuda, contiguous, device
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        return 0x1000
+
+
+@pytest.mark.parametrize("case,needle", [
+    ("short_field", "elements"),
+    ("f32_out", "float64"),
+    ("one_element_out", "float64"),
+    ("wrong_dtype", "dtype"),
+    ("host_field", "CUDA"),
+    ("strided", "contiguous"),
+    ("other_device", "cuda:1"),
+])
+def test_noalloc_binding_rejects_bad_tensors(case, needle):
+    pr, *_ = wl.random_state(2, (8, 8))
+    F = _FakeCudaTensor
+    f = [F(64), F(64), F(64)]
+    out = F(2, dtype="torch.float64")
+    if case == "short_field":
+        f[1] = F(63)
+    elif case == "f32_out":
+        out = F(2, dtype="torch.float32")
+    elif case == "one_element_out":
+        out = F(1, dtype="torch.float64")
+    elif case == "wrong_dtype":
+        f[2] = F(64, dtype="torch.float64")
+    elif case == "host_field":
+        f[0] = F(64, cuda=False)
+    elif case == "strided":
+        f[0] = F(64, contiguous=False)
+    elif case == "other_device":
+        f[2] = F(64, device="cuda:1")
+    with pytest.raises(pf.PFError, match=needle):
+        pf.energy_solute_noalloc(pr, *f, out, precision="fp32")
+    ptrs = pf._noalloc_pointers(pr, "fp32", F(64), F(64), F(64), F(2, dtype="torch.float64"))
+    assert len(ptrs) == 4
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(interp=7), "interp"),
+    (dict(lo=(5, 0, 0)), "boundary"),
+    (dict(lo=(1, 0, 0)), "periodic"),
+    (dict(H=float("inf")), "non-finite"),
+    (dict(sigma=float("nan")), "positive"),
+    (dict(lap_stencil=19), "lap_stencil"),
+    (dict(dt=float("nan")), "non-finite"),
+])
+def test_noalloc_entry_point_validates_like_pf_create(over, needle):
+    """The C entry point returns PF_EINVAL for the descriptions pf_create
+    rejects (unknown interp, an unknown or one-sided boundary code, non-finite
+    parameters), before it touches the device."""
+    pr, *_ = wl.random_state(2, (8, 8))
+    g, b, p = pf.make_structs(pr, "fp32")
+    for k, v in over.items():
+        for s in (g, b, p):
+            if hasattr(s, k):
+                if k in ("lo", "hi"):
+                    for a, x in enumerate(v):
+                        getattr(s, k)[a] = x
+                else:
+                    setattr(s, k, v)
+    dummy = ctypes.c_void_p(0x1000)
+    rc = pf.lib().pf_energy_solute_noalloc(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), 0, 0,
+                                           dummy, dummy, dummy, dummy, None)
+    assert rc == pf.PF_EINVAL
+    assert needle in pf.lib().pf_last_error(None).decode()

@@ -3,6 +3,8 @@ callers that cannot allocate device memory (their device memory is held by
 another allocator, they run on a path that must not block or fail on an
 allocation, or they have no pf_handle), checked against pf_energy and
 pf_solute_total on two calls in a row.  Collected last on purpose."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -46,9 +48,32 @@ def test_noalloc_rejects_invalid_sizes():
     pr, phi, cs, cl = wl.random_state(2, (8, 8))
     t = torch.zeros(64, dtype=torch.float32, device="cuda")
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
-    big = dict(pr, n=(1 << 16, 1 << 15))
-    with pytest.raises(pf.PFError, match="2\\^30"):
-        pf.energy_solute_noalloc(big, t, t, t, out)
+    ptr = ctypes.c_void_p(t.data_ptr())
+
+    def c_call(pr_, **over):
+        # straight through the C ABI with real device pointers: the entry point's
+        # own checks, whatever the binding checks first
+        g, b, p = pf.make_structs(pr_, "fp32")
+        for k, v in over.items():
+            setattr(p, k, v)
+        return pf.lib().pf_energy_solute_noalloc(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), 0, 0,
+                                                 ptr, ptr, ptr, ctypes.c_void_p(out.data_ptr()), None)
+
+    assert c_call(dict(pr, n=(1 << 16, 1 << 15))) == pf.PF_EINVAL
+    assert "2^30" in pf.lib().pf_last_error(None).decode()
     bad = dict(pr, lap=19)
     with pytest.raises(pf.PFError, match="lap_stencil"):
         pf.energy_solute_noalloc(bad, t, t, t, out)
+    # descriptions pf_create rejects: an unknown interpolation code, a
+    # one-sided periodic axis
+    assert c_call(pr, interp=7) == pf.PF_EINVAL
+    assert "interp" in pf.lib().pf_last_error(None).decode()
+    with pytest.raises(pf.PFError, match="periodic"):
+        pf.energy_solute_noalloc(dict(pr, bc_lo=("periodic", "noflux")), t, t, t, out)
+    # tensors that do not fit the grid or the precision never reach the kernel
+    with pytest.raises(pf.PFError, match="elements"):
+        pf.energy_solute_noalloc(pr, t, t[:63], t, out)
+    with pytest.raises(pf.PFError, match="float64"):
+        pf.energy_solute_noalloc(pr, t, t, t, out.float())
+    with pytest.raises(pf.PFError, match="float64"):
+        pf.energy_solute_noalloc(pr, t, t, t, out[:1])
