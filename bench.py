@@ -10,8 +10,10 @@ every step) is larger than the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank runs its own independent 256^3 problem on its GPU
-(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+Under torchrun (N > 1) the one 256^3 grid is cut into N z-slabs, one per rank,
+with the two ghost planes per cut exchanged over NCCL before every step
+(strong scaling); --mode replicas runs one independent grid per rank instead
+(weak scaling, no collective on the data path).  Rank 0 prints one JSON line.
 `--impl reference` times the FP64 CPU oracle (the method as plainly written)
 on this host's cores instead.
 """
@@ -55,10 +57,15 @@ def config(n, steps_note):
 # Algorithmic FP32 operations of one 3D cell-update (19-point Laplacian), counted
 # from the formulas of the step with every add, multiply, reciprocal and log as
 # one operation and a fused multiply-add as two: pointwise values 24, phase-field
-# rate 117, three faces 3 x 116, update 20.
+# rate 117, three faces 3 x 116, update 20 = 509.  Twelve of them are
+# reciprocals and logarithms (2 logs per cell, 4 reciprocals in the rate, 2 per
+# face), which run on the multi-function unit, not the FMA pipe: 497 FMA-pipe
+# operations and 12 MUFU operations per cell-update.
 OPS_PER_CELL_UPDATE = 509
+MUFU_PER_CELL_UPDATE = 12
+FMA_OPS_PER_CELL_UPDATE = OPS_PER_CELL_UPDATE - MUFU_PER_CELL_UPDATE
 BYTES_PER_CELL_UPDATE = 24          # FP32 read + write of phi, c_s, c_l (algorithmic)
-SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
+FP32_LANES, MUFU_LANES = 128, 16    # per SM and clock: FP32 FMA lanes, MUFU results
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step3d_kernel
 # launch from an ncu capture, per cell-update, and the SHA-256 of the sources
@@ -187,6 +194,201 @@ def cpu_baseline(n, max_seconds=25.0):
     return {"value": cells * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{steps} FP64 oracle steps of the full {n}^3 grid after 1 warm-up step",
             "seconds": el}
+
+
+def sm_count(device=0):
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def kv_brief(steps=500):
+    """Bounded k(V) figures for the default line.  (1) The 256-instance sweep of
+    kv_sweep_inputs for a fixed budget of `steps` steps: one batched run
+    (persistent launches in a CUDA graph) against a per-instance loop of the
+    single-handle step, launched step by step and, a stronger baseline, with
+    each instance's steps captured in a CUDA graph and replayed.  (2) Four
+    steep-gradient pulled fronts (G = 0.2 per W, D_s/D_l = 0.1, A = b = 1, V in
+    0.2..2) run to steady state by the batch's own convergence test
+    (|dk/dt| < 1e-8 per unit time after 200 W of pulling), with the steady state
+    checked by mass balance: the solid 10-20 W behind the front carries c_inf."""
+    import torch
+    from paper_2303_09671_gb300 import pf
+    lengths, vs, prs, dts, phi, cs, cl = kv_sweep_inputs()
+    f32 = [a.astype(np.float32) for a in (phi, cs, cl)]
+    K = int(steps)
+    pf.run_batch(prs[0], lengths, vs, *f32, dt=dts, max_steps=K, steps_per_launch=K,
+                 launches_per_graph=1, tol=-1.0)                      # warm-up (autotune)
+    res = pf.run_batch(prs[0], lengths, vs, *f32, dt=dts, max_steps=K, steps_per_launch=K,
+                       launches_per_graph=1, tol=-1.0)
+    batch_s = res["gpu_ms"] * 1e-3
+    stream = torch.cuda.Stream()
+    loop_s = graph_s = 0.0
+    o = 0
+    with torch.cuda.stream(stream):
+        for pr, n, dt in zip(prs, lengths, dts):
+            n = int(n)
+            src = [a[o:o + n] for a in f32]
+            o += n
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with pf.Sim(dict(pr, dt=dt), "fp32", stream=stream.cuda_stream) as s:
+                s.set_fields(*src)
+                e0.record(stream)
+                s.step(K)
+                e1.record(stream)
+                e1.synchronize()
+                loop_s += e0.elapsed_time(e1) * 1e-3
+                s.set_fields(*src)
+                s.set_clock(0, 0)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    s.step(K)
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+                e1.synchronize()
+                graph_s += e0.elapsed_time(e1) * 1e-3
+                del g
+    out = {"workload": "256 pulled fronts of kv_sweep_inputs, fixed budget", "steps": K,
+           "batch_gpu_s": batch_s, "loop_gpu_s": loop_s, "loop_graph_gpu_s": graph_s,
+           "speedup_vs_loop": loop_s / batch_s, "speedup_vs_graph_loop": graph_s / batch_s,
+           "cells_per_thread": int(res["cells_per_thread"])}
+    # steady state of steep-gradient fronts
+    k_e, vs4, n = 0.1, np.array([0.2, 0.5, 1.0, 2.0]), 2048
+    prs4, fl = [], [[], [], []]
+    for v in vs4:
+        pr, a, b, c = wl.pulled_front_1d(N=n, dx=0.5, V=float(v), k_e=k_e, D_s=0.1, A=1.0, b=1.0,
+                                         G_theta=0.2, front_cell=64)
+        prs4.append(pr)
+        for lst, x in zip(fl, (a, b, c)):
+            lst.append(x)
+    dts4 = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs4, vs4)]
+    packed = [np.concatenate(x).astype(np.float32) for x in fl]
+    t0 = time.perf_counter()
+    r = pf.run_batch(prs4[0], [n] * 4, vs4, *packed, dt=dts4, max_steps=200000, steps_per_launch=1000,
+                     launches_per_graph=4, check_every=1000, window=20.0, tol=1e-8, min_travel=200.0,
+                     want_fields=True)
+    wall = time.perf_counter() - t0
+    mb = []
+    for i in range(4):
+        f = r["phi"][i * n:(i + 1) * n].astype(np.float64)
+        j = np.where((f[:-1] >= 0.5) & (f[1:] < 0.5))[0]
+        if len(j) != 1 or j[0] < 41:
+            mb.append(None)
+            continue
+        p = f ** 3 * (6 * f * f - 15 * f + 10)
+        c = p * r["cs"][i * n:(i + 1) * n] + (1 - p) * r["cl"][i * n:(i + 1) * n]
+        mb.append(float(np.abs(c[j[0] - 40:j[0] - 20] - 1.0).max()))
+    out["steady"] = {"workload": "4 pulled fronts x 2048 cells, G=0.2/W, D_s/D_l=0.1, k_e=0.1, A=b=1, FP32",
+                     "V": vs4.tolist(), "converged": r["converged"].astype(int).tolist(),
+                     "steps": r["steps"].tolist(), "t": r["t"].tolist(), "k_v": r["k_v"].tolist(),
+                     "solid_behind_front_minus_cinf": mb, "gpu_s": r["gpu_ms"] * 1e-3, "wall_s": wall,
+                     "criterion": "|dk/dt| < 1e-8 per unit time over 20 time units, after 200 W of pulling"}
+    return out
+
+
+def adjoint_brief(steps=5000):
+    """Bounded derivative figures for the default line: d k_i / d(M_phi, A, b)
+    of the 16 pulled fronts of adjoint_inputs over `steps` FP32 steps, by the
+    tangent-linear run and by the reverse sweep, each against the forward run."""
+    from paper_2303_09671_gb300 import pf
+    lengths, vs, prs, dts, phi, cs, cl, kt = adjoint_inputs()
+    K = int(steps)
+    f32 = [a.astype(np.float32) for a in (phi, cs, cl)]
+    spl = max(1, K // 4)
+    fw = dict(dt=dts, max_steps=K, steps_per_launch=spl, launches_per_graph=4, check_every=K, tol=-1.0)
+    pf.run_batch(prs[0], lengths, vs, *f32, **dict(fw, max_steps=spl, launches_per_graph=1))     # warm-up
+    fwd = pf.run_batch(prs[0], lengths, vs, *f32, **fw)
+    out = {"workload": "16 pulled fronts x 2048 cells, V 0.05..5, A=1.1, b=1, FP32", "steps": K,
+           "forward_gpu_s": fwd["gpu_ms"] * 1e-3}
+    ref = None
+    for mode in ("tangent", "reverse"):
+        kw = dict(k_target=kt, dt=dts, mode=mode)
+        if mode == "tangent":
+            kw["steps_per_launch"] = spl
+        pf.adjoint(prs[0], lengths, vs, *f32, spl, **kw)                                          # warm-up
+        a = pf.adjoint(prs[0], lengths, vs, *f32, K, **kw)
+        out[mode] = {"gpu_s": a["gpu_ms"] * 1e-3, "cost_ratio": a["gpu_ms"] / fwd["gpu_ms"]}
+        if ref is None:
+            ref = a["dk"]
+        else:
+            out[mode]["dk_vs_tangent_max_rel"] = float(np.abs(a["dk"] - ref).max() / np.abs(ref).max())
+    return out
+
+
+def run_slabs(args, torch, dist, world, rank, local):
+    """N > 1: the one 256^3 grid cut into `world` z-slabs, one per rank; before
+    every step each rank sends its two boundary planes per cut to its
+    neighbours and imports theirs (NCCL point-to-point, 2 x 2 x 256^2 x 16 B =
+    4.2 MB per rank and step), then steps its slab.  Strong scaling: the work
+    is fixed, `value` counts the whole grid's cells."""
+    from paper_2303_09671_gb300.slabs import SlabRun
+    n = args.size
+    pr, phi, cs, cl = workload(n)
+    cells = int(np.prod(pr["n"]))
+    run = SlabRun(pr, "fp32", rank, world, dist)
+    z0, nzl = run.z0, run.nzl
+    own = [np.ascontiguousarray(a[z0:z0 + nzl], dtype=np.float32) for a in (phi, cs, cl)]
+    del phi, cs, cl
+    run.set_fields(*own)
+    S0 = run.solute_total()
+    for _ in range(args.warmup):
+        run.step(1)
+    dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            run.step(1)
+        ev1.record(stream)
+        ev1.synchronize()
+    dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    drift = abs(run.solute_total() - S0) / abs(S0)
+    # end to end: each rank uploads its slab from pinned host memory, exchanges,
+    # steps, and reads its slab back
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in own]
+    back = [torch.empty(a.shape, dtype=torch.float32).pin_memory().numpy() for a in own]
+    ke = max(1, args.e2e_steps)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        run.set_fields(*pinned)
+        run.step(1)
+        run.sim.get_fields(out_host=back)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    ms_max, e2e_max = max_over_ranks([ms, e2e_s], dist, device="cuda")
+    if rank == 0:
+        value = cells * args.steps / (ms_max * 1e-3)
+        hbm_peak, sm_mhz, how = load_peaks()
+        sms = sm_count(local)
+        own_cells = int(np.prod(own[0].shape))
+        step_s = ms / args.steps * 1e-3
+        achieved = FMA_OPS_PER_CELL_UPDATE * own_cells / step_s / 1e12
+        alu_peak = sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config(n, {"parallelism": f"z-slabs x{world}: NCCL send/recv of 2 ghost planes per cut "
+                                                "and step (pf_get_halo / pf_set_halo)",
+                                 "scaling_unit": "one grid over all ranks"}),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "traffic_note": "rank 0's slab; the step time includes the halo exchange",
+                         "kernel": "step3d_kernel<float,32,16,19-point>",
+                         "ops_per_cell_update": FMA_OPS_PER_CELL_UPDATE},
+            "e2e": {"value": cells * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * cells,
+                    "d2h_bytes_per_step": 3 * 4 * cells, "steps": ke},
+            "gpu_launches": args.steps, "solute_drift": drift, "clocks": clk.summary(),
+        }
+        print(json.dumps(out), flush=True)
+    run.close()
+    dist.destroy_process_group()
+    return 0
 
 
 def run_reference(args):
@@ -461,8 +663,13 @@ def main():
     ap.add_argument("--calibrate", type=int, default=0,
                     help="adjoint workload: Adam iterations of the k(V) calibration after the timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="leave out the bounded kv_sweep and adjoint keys of the default line")
     ap.add_argument("--workload", default="sphere3d",
                     choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d"])
+    ap.add_argument("--mode", default="slabs", choices=["slabs", "replicas"],
+                    help="N > 1: one grid cut into z-slabs with a halo exchange every step (strong "
+                         "scaling), or one independent grid per rank (weak scaling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "kv-sweep":
@@ -483,8 +690,13 @@ def main():
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
+        import datetime
         import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
+        # a bounded timeout: a rank that stops answering ends the run with an
+        # error instead of holding every GPU
+        dist.init_process_group("nccl", init_method="env://", timeout=datetime.timedelta(seconds=300))
+        if args.mode == "slabs":
+            return run_slabs(args, torch, dist, world, rank, local)
 
     def barrier():
         if dist is not None:
@@ -517,35 +729,52 @@ def main():
         drift = abs(S1 - S0) / abs(S0)
 
         # end to end through the public API with host buffers: every step uploads
-        # the state from pinned host memory, steps, and reads back the solute total
+        # the state (phi, c_s, c_l) from pinned host memory, steps, and reads the
+        # stepped fields back into pinned host memory
         pinned = [torch.from_numpy(a).pin_memory() for a in f32]
         host_views = [p.numpy() for p in pinned]
+        back = [torch.empty(a.shape, dtype=torch.float32).pin_memory().numpy() for a in f32]
         ke = max(1, args.e2e_steps)
-        # each step's result is read back asynchronously into page-locked
-        # memory, so that the next step's upload is queued without a host stall
-        results = torch.zeros(ke, dtype=torch.float64).pin_memory().numpy()
         barrier()
         t0 = time.perf_counter()
         for i in range(ke):
             sim.set_fields_step(*host_views, n=1)   # upload overlapped with the step
-            sim.solute_total_async(results, i)
+            sim.get_fields(out_host=back)           # the stepped fields, to the host
         stream.synchronize()
         e2e_s = time.perf_counter() - t0
+        if not all(np.isfinite(b).all() for b in back):
+            raise RuntimeError("non-finite field in the end-to-end leg")
+        # the same with only the solute total read back (8 bytes a step), each
+        # result queued into page-locked memory so that the next upload is
+        # queued without a host stall
+        results = torch.zeros(ke, dtype=torch.float64).pin_memory().numpy()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(ke):
+            sim.set_fields_step(*host_views, n=1)
+            sim.solute_total_async(results, i)
+        stream.synchronize()
+        e2e_solute_s = time.perf_counter() - t0
         if not np.isfinite(results).all():
             raise RuntimeError("non-finite solute total in the end-to-end leg")
         sim.close()
 
-    ms_max, e2e_max = max_over_ranks([ms, e2e_s], dist, device="cuda")
+    ms_max, e2e_max, e2e_sol_max = max_over_ranks([ms, e2e_s, e2e_solute_s], dist, device="cuda")
     value = weak_scaling_rate(cells, args.steps, world, ms_max * 1e-3)
     e2e_value = weak_scaling_rate(cells, ke, world, e2e_max)
+    e2e_sol_value = weak_scaling_rate(cells, ke, world, e2e_sol_max)
 
     if rank == 0:
         hbm_peak, sm_mhz, how = load_peaks()
+        sms = sm_count(local)
         launch_s = ms / args.steps * 1e-3
         achieved_gbs = BYTES_PER_CELL_UPDATE * cells / launch_s / 1e9
-        # FP32 ALU peak: every lane issuing one FMA (2 operations) per clock
-        alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-        achieved_tops = OPS_PER_CELL_UPDATE * cells / launch_s / 1e12
+        # FP32 FMA-pipe peak: every lane issuing one FMA (2 operations) per clock;
+        # the reciprocals and logarithms run beside it on the MUFU
+        alu_peak = sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        achieved_tops = FMA_OPS_PER_CELL_UPDATE * cells / launch_s / 1e12
+        mufu_peak = sms * MUFU_LANES * sm_mhz * 1e6 / 1e12
+        mufu_achieved = MUFU_PER_CELL_UPDATE * cells / launch_s / 1e12
         traffic = step3d_traffic(cells)
         cap = TRAFFIC_CAPTURE["captured_grid"]
         traffic_note = ("kernel sources changed since the capture" if traffic is None else
@@ -559,18 +788,31 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": achieved_tops / alu_peak, "traffic": traffic,
                          "traffic_note": traffic_note,
-                         "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                         "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_mhz:.0f} MHz",
                          "kernel": "step3d_kernel<float,32,16,19-point>",
-                         "ops_per_cell_update": OPS_PER_CELL_UPDATE},
+                         "ops_per_cell_update": FMA_OPS_PER_CELL_UPDATE,
+                         "ops_note": (f"{OPS_PER_CELL_UPDATE} algorithmic FP32 operations per cell-update, "
+                                      f"of which {MUFU_PER_CELL_UPDATE} reciprocals/logarithms run on the MUFU "
+                                      "(see mufu) and the rest on the FMA pipe"),
+                         "mufu": {"ops_per_cell_update": MUFU_PER_CELL_UPDATE, "achieved": mufu_achieved,
+                                  "peak": mufu_peak, "frac": mufu_achieved / mufu_peak, "unit": "Top/s",
+                                  "peak_source": f"derived: {sms} SMs x {MUFU_LANES} MUFU results x {sm_mhz:.0f} MHz"}},
             "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved_gbs / hbm_peak, "peak_source": how,
                              "bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * cells,
-                    "d2h_bytes_per_step": 8, "steps": ke},
+                    "d2h_bytes_per_step": 3 * 4 * cells, "steps": ke,
+                    "path": "pf_set_fields_step (upload overlapped with the step) + pf_get_fields to pinned host memory"},
+            "e2e_solute_only": {"value": e2e_sol_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * cells,
+                                "d2h_bytes_per_step": 8, "steps": ke,
+                                "path": "pf_set_fields_step + pf_solute_total_async (8-byte result per step)"},
             "gpu_launches": args.steps,
             "solute_drift": drift,
             "clocks": clk.summary(),
         }
+        if world == 1 and not args.no_secondary:
+            out["kv_sweep"] = kv_brief()
+            out["adjoint"] = adjoint_brief()
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(n)
         print(json.dumps(out), flush=True)

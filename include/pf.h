@@ -52,7 +52,7 @@ enum {
     PF_ETIMEOUT = -5,      /* a bounded device wait ran out */
     PF_EUNSUPPORTED = -6   /* combination not supported by this build */
 };
-enum { PF_BC_NOFLUX = 0, PF_BC_PERIODIC = 1, PF_BC_DIRICHLET = 2 };
+enum { PF_BC_NOFLUX = 0, PF_BC_PERIODIC = 1, PF_BC_DIRICHLET = 2, PF_BC_HALO = 3 };
 enum { PF_FP32 = 0, PF_FP64 = 1 };
 enum { PF_HOST = 0, PF_DEVICE = 1 };
 enum { PF_INTERP_QUINTIC = 0, PF_INTERP_CUBIC = 1 };  /* h(phi), Sec. "Choice of interpolation functions" */
@@ -72,7 +72,11 @@ typedef struct {
  * PF_BC_PERIODIC wrap (both sides of the axis must be periodic),
  * PF_BC_DIRICHLET fixed ghosts phi = dir_phi, c_s = dir_cs, c_l = dir_cl, whose
  *                phase-field rate is zero.  The same values fill the fresh
- *                layer of the moving window. */
+ *                layer of the moving window.
+ * PF_BC_HALO     (3D, z sides only) the side borders another slab of a grid
+ *                decomposed along z: the two ghost planes beyond it are held in
+ *                the handle and imported with pf_set_halo before every step
+ *                (see pf_get_halo). */
 typedef struct {
     int lo[3], hi[3];
     double dir_phi, dir_cs, dir_cl;
@@ -162,6 +166,41 @@ int pf_step(pf_handle* h, int64_t n);
  * is undefined until the next pf_set_fields. */
 int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void* cl, int where,
                        int64_t n);
+
+/* ------------------------------------------------------------------------
+ * Domain decomposition along z (3D): a grid split into slabs of whole x-y
+ * planes, one handle per slab, each slab's z sides that border another slab
+ * set to PF_BC_HALO.  The step's stencil reaches two planes across a face
+ * (the face fluxes of Eqs. cs_nonvar / cl_nonvar need the phase-field rate of
+ * the cells on both sides, which needs their neighbours), so before every
+ * step each halo side imports the two planes beyond it from the neighbouring
+ * slab: my low ghosts are the lower slab's two highest planes, my high ghosts
+ * the upper slab's two lowest.  With the halos imported, a slab computes its
+ * cells bit for bit as the undecomposed grid does, and the sums of the slabs'
+ * pf_energy and pf_solute_total are the grid's (each gradient pair across a
+ * slab boundary counted half in each slab).
+ *
+ * pf_halo_bytes: bytes of one side's halo (two planes of every state word:
+ *   phi, c, d and, in FP32, the low word of c; 2 n[0] n[1] values each).
+ * pf_get_halo: copy the two outermost planes of the current state at `side`
+ *   (0 = low z, planes 0 and 1; 1 = high z, planes n[2]-2 and n[2]-1) into
+ *   buf: field by field in the order above, each field's two planes in
+ *   increasing z, x fastest, the handle's element type.
+ * pf_set_halo: import the two ghost planes beyond `side` (low: planes -2, -1;
+ *   high: n[2], n[2]+1) from buf, laid out as pf_get_halo writes them.
+ * where = PF_DEVICE (device memory, stream-ordered) or PF_HOST (any host
+ * memory; the call synchronises the stream).  `side` must be a PF_BC_HALO
+ * side of the handle, else PF_EINVAL.
+ *
+ * On a handle with a halo side: pf_step advances one step at a time (n <= 1)
+ * and needs every halo side imported since the last pf_set_fields or step;
+ * pf_energy needs the same (its gradient pairs reach the ghost planes);
+ * pf_solute_total, pf_front, pf_get_fields and pf_set_fields read the slab's
+ * own cells only; pf_set_fields_step and pf_step_energies return PF_EINVAL.
+ * ------------------------------------------------------------------------ */
+int pf_halo_bytes(pf_handle* h, int64_t* bytes);
+int pf_get_halo(pf_handle* h, int side, void* buf, int where);
+int pf_set_halo(pf_handle* h, int side, const void* buf, int where);
 
 /* Discrete free energy of Eq. model1.1 for the current state, FP64:
  *   F_h = dV sum_i [H f_dw(phi_i) + p_i f_s,i + (1-p_i) f_l,i]

@@ -27,6 +27,13 @@ struct pf_handle {
     static constexpr int OV_STREAMS = 4;
     cudaStream_t ov[OV_STREAMS] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ov_ev;
+    // z-slab of a decomposed grid: which z sides are halo sides, whether each
+    // has been imported for the current state, and the padded allocations
+    // (two ghost planes below and above; buf[b] points at plane 0 of them)
+    bool halo[2] = {false, false};
+    bool halo_set[2] = {false, false};
+    void* alloc[2][5] = {{nullptr, nullptr, nullptr, nullptr, nullptr},
+                         {nullptr, nullptr, nullptr, nullptr, nullptr}};
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
     int ovchunk = 16;            // z planes per slab and CTA in pf_set_fields_step
     bool generic = false;        // run 2D / 3D through the generic kernel (cross-check)
@@ -100,7 +107,9 @@ std::string validate_problem(const pf_grid* g, const pf_bc* bc, const pf_params*
         if (a < g->dim) {
             if (g->n[a] < 3) return "each active axis needs at least 3 cells";
             const int lo = bc->lo[a], hi = bc->hi[a];
-            if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return "unknown boundary condition";
+            if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return "unknown boundary condition";
+            if ((lo == PF_BC_HALO || hi == PF_BC_HALO) && !(stepping && g->dim == 3 && a == 2))
+                return "halo sides are only for the z ends of a 3D handle";
             if ((lo == PF_BC_PERIODIC) != (hi == PF_BC_PERIODIC))
                 return "periodic boundaries must be set on both sides of an axis";
         } else if (g->n[a] != 1) {
@@ -203,19 +212,26 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     if (const char* oc = std::getenv("PF_OVCHUNK")) h->ovchunk = std::atoi(oc);
     if (const char* g = std::getenv("PF_GENERIC")) h->generic = std::atoi(g) != 0;   // cross-check kernel
 
-    const size_t bytes = (size_t)P.cells() * P.elem();
+    h->halo[0] = P.bc_lo[2] == PF_BC_HALO;
+    h->halo[1] = P.bc_hi[2] == PF_BC_HALO;
+    // a slab keeps two ghost planes below and above its own planes
+    const size_t plane = (size_t)P.n[0] * P.n[1];
+    const size_t pad = (h->halo[0] || h->halo[1]) ? 2 * plane : 0;
+    const size_t bytes = ((size_t)P.cells() + 2 * pad) * P.elem();
     for (int b = 0; b < 2; ++b) {
         void** slots[5] = {&h->buf[b].phi, &h->buf[b].c, &h->buf[b].d, &h->buf[b].clo, &h->buf[b].plo};
         // FP32 keeps the low word of c, and in 1D also that of phi
         const int nf = (P.precision == PF_FP32) ? (P.dim == 1 ? 5 : 4) : 3;
         for (int f = 0; f < nf; ++f) {
-            cudaError_t e = cudaMalloc(slots[f], bytes);
+            cudaError_t e = cudaMalloc(&h->alloc[b][f], bytes);
             if (e != cudaSuccess) {
                 cudaGetLastError();
+                h->alloc[b][f] = nullptr;
                 pf_destroy(h);
                 return fail(nullptr, PF_ENOMEM, std::string("device allocation failed: ") +
                                                     cudaGetErrorString(e));
             }
+            *slots[f] = static_cast<char*>(h->alloc[b][f]) + pad * P.elem();
         }
     }
     cudaError_t e = cudaMalloc(&h->scratch, pf::diag_scratch_doubles(P) * sizeof(double));
@@ -234,11 +250,9 @@ void pf_destroy(pf_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    for (int b = 0; b < 2; ++b) {
-        void* slots[5] = {h->buf[b].phi, h->buf[b].c, h->buf[b].d, h->buf[b].clo, h->buf[b].plo};
-        for (void* p : slots)
+    for (int b = 0; b < 2; ++b)
+        for (void* p : h->alloc[b])
             if (p) cudaFree(p);
-    }
     if (h->scratch) cudaFree(h->scratch);
     if (h->dres) cudaFree(h->dres);
     if (h->hres) cudaFreeHost(h->hres);
@@ -269,6 +283,7 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
     cudaError_t e = pf::launch_to_state(h->P, src[0], src[1], src[2], h->buf[h->cur], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
     h->have_front = false;
+    h->halo_set[0] = h->halo_set[1] = false;
     if (where == PF_HOST) {
         // the caller may reuse its host memory as soon as we return
         e = cudaStreamSynchronize(h->stream);
@@ -283,6 +298,8 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
+    if (h->halo[0] || h->halo[1])
+        return fail(h, PF_EINVAL, "a slab with halo sides sets its fields, imports its halos, then steps");
     const pf::HostProblem& P = h->P;
     const void* src[3] = {phi, cs, cl};
     const bool readable = where == PF_DEVICE || device_views(src);
@@ -407,6 +424,12 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
 int pf_step(pf_handle* h, int64_t n) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
+    if (h->halo[0] || h->halo[1]) {
+        if (n > 1) return fail(h, PF_EINVAL, "a slab with halo sides steps one step at a time");
+        if (n == 1 && ((h->halo[0] && !h->halo_set[0]) || (h->halo[1] && !h->halo_set[1])))
+            return fail(h, PF_EINVAL, "halo not imported since the last step or pf_set_fields");
+        h->halo_set[0] = h->halo_set[1] = false;
+    }
     const pf::HostProblem& P = h->P;
     for (int64_t s = 0; s < n; ++s) {
         const pf::Fields& in = h->buf[h->cur];
@@ -455,6 +478,8 @@ static int energy_solute(pf_handle* h, bool with_energy) {
 int pf_energy(pf_handle* h, double* F) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!F) return fail(h, PF_EINVAL, "null output");
+    if ((h->halo[0] && !h->halo_set[0]) || (h->halo[1] && !h->halo_set[1]))
+        return fail(h, PF_EINVAL, "halo not imported: the energy's gradient pairs reach the ghost planes");
     int rc = energy_solute(h, true);
     if (rc) return rc;
     *F = h->hres[0];
@@ -465,6 +490,7 @@ int pf_energy(pf_handle* h, double* F) {
 int pf_step_energies(pf_handle* h, int64_t n, double* F) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
+    if (h->halo[0] || h->halo[1]) return fail(h, PF_EINVAL, "not for a slab with halo sides");
     if (n > 0 && !F) return fail(h, PF_EINVAL, "null output");
     if (n == 0) return PF_OK;
     if (h->rec_cap < n) {
@@ -596,6 +622,57 @@ int pf_front(pf_handle* h, double* x_front, double* v_front, double* c_max) {
     h->last_t = t;
     if (!std::isfinite(*c_max)) return fail(h, PF_ENONFINITE, "non-finite concentration");
     return PF_OK;
+}
+
+// ---------------------------------------------------------------- halos
+
+// the state words of a halo: phi, c, d and (FP32) the low word of c
+static int halo_nfields(const pf_handle* h) { return h->P.precision == PF_FP32 ? 4 : 3; }
+
+int pf_halo_bytes(pf_handle* h, int64_t* bytes) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!bytes) return fail(h, PF_EINVAL, "null output");
+    *bytes = (int64_t)halo_nfields(h) * 2 * h->P.n[0] * h->P.n[1] * (int64_t)h->P.elem();
+    return PF_OK;
+}
+
+static int halo_copy(pf_handle* h, int side, void* buf, int where, bool import) {
+    if (side != 0 && side != 1) return fail(h, PF_EINVAL, "side must be 0 (low z) or 1 (high z)");
+    if (!h->halo[side]) return fail(h, PF_EINVAL, "that z side is not a halo side");
+    if (!buf) return fail(h, PF_EINVAL, "null buffer");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    const pf::HostProblem& P = h->P;
+    const size_t plane = (size_t)P.n[0] * P.n[1] * P.elem();
+    // first plane of the two: own planes 0 / nz-2 (export), ghosts -2 / nz (import)
+    const int64_t z = import ? (side == 0 ? -2 : P.n[2]) : (side == 0 ? 0 : P.n[2] - 2);
+    const pf::Fields& F = h->buf[h->cur];
+    void* const f[4] = {F.phi, F.c, F.d, F.clo};
+    const int nf = halo_nfields(h);
+    const cudaMemcpyKind kind = where == PF_DEVICE ? cudaMemcpyDeviceToDevice
+                                                   : (import ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    for (int k = 0; k < nf; ++k) {
+        char* state = static_cast<char*>(f[k]) + z * (int64_t)plane;
+        char* ext = static_cast<char*>(buf) + (size_t)k * 2 * plane;
+        cudaError_t e = import ? cudaMemcpyAsync(state, ext, 2 * plane, kind, h->stream)
+                               : cudaMemcpyAsync(ext, state, 2 * plane, kind, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "halo copy");
+    }
+    if (where == PF_HOST) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+    if (import) h->halo_set[side] = true;
+    return PF_OK;
+}
+
+int pf_get_halo(pf_handle* h, int side, void* buf, int where) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    return halo_copy(h, side, buf, where, false);
+}
+
+int pf_set_halo(pf_handle* h, int side, const void* buf, int where) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    return halo_copy(h, side, const_cast<void*>(buf), where, true);
 }
 
 int pf_get_clock(pf_handle* h, int64_t* step, int64_t* shifts) {

@@ -67,7 +67,7 @@ __device__ __forceinline__ double fetch_phi(const DiagConsts& C, const T* phi, i
     int mi = map_coord(i, C.n[0], C.bc_lo[0], C.bc_hi[0]);
     int mj = (C.dim >= 2) ? map_coord(j, C.n[1], C.bc_lo[1], C.bc_hi[1]) : 0;
     int mk = (C.dim >= 3) ? map_coord(k, C.n[2], C.bc_lo[2], C.bc_hi[2]) : 0;
-    if (mi < 0 || mj < 0 || mk < 0) return C.dir_phi;
+    if (mi < 0 || mj < 0 || mk == DIR_GHOST) return C.dir_phi;
     return (double)phi[((long long)mk * C.n[1] + mj) * C.n[0] + mi];
 }
 

@@ -7,7 +7,15 @@
 
 namespace pf {
 
-enum { BC_NOFLUX = 0, BC_PERIODIC = 1, BC_DIRICHLET = 2 };
+enum { BC_NOFLUX = 0, BC_PERIODIC = 1, BC_DIRICHLET = 2, BC_HALO = 3 };
+
+// map_coord's marker for a Dirichlet ghost.  A halo side (the z ends of a slab
+// of a decomposed grid) maps its ghost planes to their own, negative or
+// >= n, indices: the state arrays hold the two ghost planes beyond such a
+// side, imported from the neighbouring slab.  So tests for a Dirichlet ghost
+// along z compare with DIR_GHOST; along x and y, where no side is a halo, any
+// negative result is one.
+constexpr int DIR_GHOST = -0x7fffffff - 1;
 
 // Parameters in the kernel's arithmetic type T.
 template <typename T>
@@ -60,14 +68,16 @@ struct Clock {
 };
 
 // Map a possibly-ghost coordinate onto the interior (noflux: mirror about
-// the boundary face; periodic: wrap); -1 marks a Dirichlet ghost.  Cells
-// further than the ghost width from the domain (only present in partial
-// tiles, never used by interior cells) are clamped to keep loads in bounds.
+// the boundary face; periodic: wrap; halo: the ghost plane itself, held in the
+// state arrays); DIR_GHOST marks a Dirichlet ghost.  Cells further than the
+// ghost width from the domain (only present in partial tiles, never used by
+// interior cells) are clamped to keep loads in bounds.
 __device__ __forceinline__ int map_coord(int i, int n, int lo, int hi) {
     if (i >= 0 && i < n) return i;
     int bc = (i < 0) ? lo : hi;
     int m;
-    if (bc == BC_DIRICHLET) return -1;
+    if (bc == BC_DIRICHLET) return DIR_GHOST;
+    if (bc == BC_HALO) return i;
     if (bc == BC_PERIODIC) {
         m = i % n;
         if (m < 0) m += n;

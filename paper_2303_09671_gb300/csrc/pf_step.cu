@@ -139,7 +139,7 @@ step_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in,
         bool dirz = false;
         if constexpr (DIM == 3) {
             mz = map_coord(z, nz, C.bc_lo[2], C.bc_hi[2]);
-            dirz = (mz < 0);
+            dirz = (mz == DIR_GHOST);
         }
         for (int h = tid; h < L::HP; h += nthreads) {
             const int hx = h % L::HX, hy = h / L::HX;
@@ -179,7 +179,7 @@ step_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in,
     auto rates_plane = [&](int z, int sM, int s0, int sP, int g) {
         const T theta_base = K.theta0;
         bool dirz = false;
-        if constexpr (DIM == 3) dirz = (map_coord(z, nz, C.bc_lo[2], C.bc_hi[2]) < 0);
+        if constexpr (DIM == 3) dirz = (map_coord(z, nz, C.bc_lo[2], C.bc_hi[2]) == DIR_GHOST);
         for (int r = tid; r < L::RP; r += nthreads) {
             const int rx = r % L::RX, ry = r / L::RX;
             const int hx = rx + 1, hy = (DIM >= 2) ? ry + 1 : 0;

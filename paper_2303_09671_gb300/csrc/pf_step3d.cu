@@ -169,7 +169,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 T* dst = sR + l * NHP + h;
-                if (mz >= 0 && hoff[j][l] >= 0) {
+                if (mz != DIR_GHOST && hoff[j][l] >= 0) {
                     const long long gi = (long long)mz * sz + hoff[j][l];
                     cp_async(dst, phi_in + gi);
                     cp_async(dst + 2 * NHP, c_in + gi);
@@ -224,7 +224,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
 
     // ---- B: dx^2 phidot of one ring pair cell of plane z -> sD[z & 1][r]
     auto rate_of = [&](int z, int dsc, T xc) -> V {
-        const bool ghost_z = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) < 0;
+        const bool ghost_z = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) == DIR_GHOST;
         const V* P0 = sP + slot3(z) * HP;
         const V* PM = sP + slot3(z - 1) * HP;
         const V* PP = sP + slot3(z + 1) * HP;

@@ -19,7 +19,7 @@ from . import build as _build
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ETIMEOUT, PF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 PF_HOST, PF_DEVICE = 0, 1
-BC = {"noflux": 0, "periodic": 1, "dirichlet": 2}
+BC = {"noflux": 0, "periodic": 1, "dirichlet": 2, "halo": 3}
 PRECISION = {"fp32": 0, "fp64": 1}
 
 _lock = threading.Lock()
@@ -108,6 +108,9 @@ _SIGS = {
     "pf_energy_solute_noalloc": (ctypes.c_int, [ctypes.POINTER(pf_grid), ctypes.POINTER(pf_bc),
                                                 ctypes.POINTER(pf_params), ctypes.c_int64, ctypes.c_int64,
                                                 _VP, _VP, _VP, _VP, _VP]),
+    "pf_halo_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "pf_get_halo": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
+    "pf_set_halo": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
     "pf_last_error": (ctypes.c_char_p, [_VP]),
     "pf_destroy": (None, [_VP]),
 }
@@ -220,12 +223,20 @@ class Sim:
         ptrs, where, _keep = self._field_ptrs(phi, cs, cl)
         _check(lib().pf_set_fields_step(self._h, *ptrs, where, int(n)), self._h)
 
-    def get_fields(self, out=None):
-        """Return (phi, cs, cl) as numpy arrays, or fill the given CUDA tensors."""
+    def get_fields(self, out=None, out_host=None):
+        """Return (phi, cs, cl) as numpy arrays, or fill the given CUDA tensors
+        (out), or the given host arrays (out_host: contiguous numpy arrays of the
+        grid shape and the handle's dtype, page-locked for a direct copy)."""
         if out is not None:
             ptrs = [_VP(a.data_ptr()) for a in out]
             _check(lib().pf_get_fields(self._h, *ptrs, PF_DEVICE), self._h)
             return out
+        if out_host is not None:
+            for a in out_host:
+                if a.shape != self.shape or a.dtype != self.dtype or not a.flags.c_contiguous:
+                    raise ValueError("out_host arrays must be contiguous, of the grid shape and dtype")
+            _check(lib().pf_get_fields(self._h, *[_VP(a.ctypes.data) for a in out_host], PF_HOST), self._h)
+            return tuple(out_host)
         arrs = [np.empty(self.shape, dtype=self.dtype) for _ in range(3)]
         _check(lib().pf_get_fields(self._h, *[_VP(a.ctypes.data) for a in arrs], PF_HOST), self._h)
         return tuple(arrs)
@@ -263,6 +274,33 @@ class Sim:
         x, v, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().pf_front(self._h, ctypes.byref(x), ctypes.byref(v), ctypes.byref(c)), self._h)
         return x.value, v.value, c.value
+
+    # -- z-slab halos (a handle whose z sides are "halo")
+    def halo_bytes(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().pf_halo_bytes(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def _halo_buf(self, buf):
+        if hasattr(buf, "data_ptr"):
+            if not buf.is_cuda or not buf.is_contiguous() or buf.numel() * buf.element_size() != self.halo_bytes():
+                raise ValueError("halo buffer: a contiguous CUDA tensor of halo_bytes() bytes")
+            return _VP(buf.data_ptr()), PF_DEVICE
+        if not buf.flags.c_contiguous or buf.nbytes != self.halo_bytes():
+            raise ValueError("halo buffer: a contiguous host array of halo_bytes() bytes")
+        return _VP(buf.ctypes.data), PF_HOST
+
+    def get_halo(self, side: int, buf):
+        """Export the two outermost planes at z side 0 (low) or 1 (high) into
+        buf (a CUDA tensor or a host array of halo_bytes() bytes)."""
+        ptr, where = self._halo_buf(buf)
+        _check(lib().pf_get_halo(self._h, int(side), ptr, where), self._h)
+        return buf
+
+    def set_halo(self, side: int, buf):
+        """Import the two ghost planes beyond z side 0 (low) or 1 (high)."""
+        ptr, where = self._halo_buf(buf)
+        _check(lib().pf_set_halo(self._h, int(side), ptr, where), self._h)
 
     @property
     def clock(self):

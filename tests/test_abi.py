@@ -210,3 +210,16 @@ def test_noalloc_entry_point_validates_like_pf_create(over, needle):
                                            dummy, dummy, dummy, dummy, None)
     assert rc == pf.PF_EINVAL
     assert needle in pf.lib().pf_last_error(None).decode()
+
+
+@pytest.mark.parametrize("dim,axis,needle", [(3, 0, "halo"), (3, 1, "halo"), (2, 1, "halo")])
+def test_halo_sides_only_on_3d_z(dim, axis, needle):
+    """PF_BC_HALO (the cut between two slabs of a grid decomposed along z) is
+    accepted on the z sides of a 3D handle only."""
+    n = (16, 12, 10)[:dim]
+    pr, *_ = wl.random_state(dim, n)
+    g, b, p = pf.make_structs(pr, "fp32")
+    b.lo[axis] = 3
+    h = ctypes.c_void_p()
+    rc = pf.lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == pf.PF_EINVAL and needle in pf.lib().pf_last_error(None).decode()
