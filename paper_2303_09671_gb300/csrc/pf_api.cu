@@ -214,10 +214,12 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
 
     h->halo[0] = P.bc_lo[2] == PF_BC_HALO;
     h->halo[1] = P.bc_hi[2] == PF_BC_HALO;
-    // a slab keeps two ghost planes below and above its own planes
-    const size_t plane = (size_t)P.n[0] * P.n[1];
-    const size_t pad = (h->halo[0] || h->halo[1]) ? 2 * plane : 0;
-    const size_t bytes = ((size_t)P.cells() + 2 * pad) * P.elem();
+    // a slab keeps two ghost planes below and above its own planes; the space
+    // below is rounded up to 256 bytes so that plane 0 keeps cudaMalloc's
+    // alignment (the FP32 solute reduction reads c and c_lo as float4)
+    const size_t ghost_bytes = (h->halo[0] || h->halo[1]) ? 2 * (size_t)P.n[0] * P.n[1] * P.elem() : 0;
+    const size_t lead = (ghost_bytes + 255) / 256 * 256;
+    const size_t bytes = lead + (size_t)P.cells() * P.elem() + ghost_bytes;
     for (int b = 0; b < 2; ++b) {
         void** slots[5] = {&h->buf[b].phi, &h->buf[b].c, &h->buf[b].d, &h->buf[b].clo, &h->buf[b].plo};
         // FP32 keeps the low word of c, and in 1D also that of phi
@@ -231,7 +233,7 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
                 return fail(nullptr, PF_ENOMEM, std::string("device allocation failed: ") +
                                                     cudaGetErrorString(e));
             }
-            *slots[f] = static_cast<char*>(h->alloc[b][f]) + pad * P.elem();
+            *slots[f] = static_cast<char*>(h->alloc[b][f]) + lead;
         }
     }
     cudaError_t e = cudaMalloc(&h->scratch, pf::diag_scratch_doubles(P) * sizeof(double));

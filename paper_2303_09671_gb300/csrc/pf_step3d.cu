@@ -188,20 +188,20 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         if (in_lo) {
             cp_async(dst, c_in + gi);
             cp_async(dst + 2 * NT, d_in + gi);
-            if (clo_in != nullptr) cp_async(dst + 4 * NT, clo_in + gi);
+            if constexpr (sizeof(T) == 4) cp_async(dst + 4 * NT, clo_in + gi);
         }
         if (in_hi) {
             cp_async(dst + NT, c_in + gi + nx);
             cp_async(dst + 3 * NT, d_in + gi + nx);
-            if (clo_in != nullptr) cp_async(dst + 5 * NT, clo_in + gi + nx);
+            if constexpr (sizeof(T) == 4) cp_async(dst + 5 * NT, clo_in + gi + nx);
         }
     };
     // staged plane z into the rings
-    auto store_plane = [&](int z) {
-        Q* A = sA + (z & 3) * HP;
-        Q* B = sB + (z & 3) * HP;
-        Q* C = sC + slot3(z) * HP;
-        V* P = sP + slot3(z) * HP;
+    auto store_plane = [&](int oa, int oc) {
+        Q* A = sA + oa;
+        Q* B = sB + oa;
+        Q* C = sC + oc;
+        V* P = sP + oc;
 #pragma unroll
         for (int j = 0; j < L::JH; ++j) {
             const int hl = tid + j * NT;
@@ -223,15 +223,16 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
 
     // ---- B: dx^2 phidot of one ring pair cell of plane z -> sD[z & 1][r]
-    auto rate_of = [&](int z, int dsc, T xc) -> V {
-        const bool ghost_z = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) == DIR_GHOST;
-        const V* P0 = sP + slot3(z) * HP;
-        const V* PM = sP + slot3(z - 1) * HP;
-        const V* PP = sP + slot3(z + 1) * HP;
-        const Q* B0 = sB + (z & 3) * HP;
-        const Q* BM = sB + ((z - 1) & 3) * HP;
-        const Q* BP = sB + ((z + 1) & 3) * HP;
-        const Q* C0 = sC + slot3(z) * HP;
+    // rate of plane z: ring offsets of planes z-1, z, z+1 (A/B rings: am, a0, ap;
+    // C/P rings: cm, c0, cp)
+    auto rate_of = [&](bool ghost_z, int am, int a0, int ap, int cm, int c0, int cp, int dsc, T xc) -> V {
+        const V* P0 = sP + c0;
+        const V* PM = sP + cm;
+        const V* PP = sP + cp;
+        const Q* B0 = sB + a0;
+        const Q* BM = sB + am;
+        const Q* BP = sB + ap;
+        const Q* C0 = sC + c0;
         const int h = dsc & 0xfff;
         const int hS = ((dsc >> 14) & 1) ? h : h - HX;   // first pair row: row below unused
         const int hN = ((dsc >> 15) & 1) ? h : h + HX;   // last pair row: row above unused
@@ -291,7 +292,14 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         }
         return pd;
     };
-    auto rate_cell = [&](int z, int dsc, T xc, int r) { sD[(z & 1) * RP + r] = rate_of(z, dsc, xc); };
+    auto offA = [&](int z) { return (z & 3) * HP; };
+    auto offC = [&](int z) { return slot3(z) * HP; };
+    auto offD = [&](int z) { return (z & 1) * RP; };
+    auto ghost = [&](int z) { return map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) == DIR_GHOST; };
+    auto rate_z = [&](int z, int dsc, T xc) -> V {
+        return rate_of(ghost(z), offA(z - 1), offA(z), offA(z + 1), offC(z - 1), offC(z), offC(z + 1), dsc, xc);
+    };
+    auto rate_cell = [&](int z, int dsc, T xc, int r) { sD[offD(z) + r] = rate_z(z, dsc, xc); };
     auto rates_plane = [&](int z) {
         rate_cell(z, own_dsc, own_xc, own_r);
         if (bor_r >= 0) rate_cell(z, bor_dsc, bor_xc, bor_r);
@@ -371,29 +379,29 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
                                vadd(d0, d1), n, t1, t2, Fc, Fd);
     };
     // single faces (the tile's low x and low y edges, the z face below the chunk)
-    auto xface = [&](int z, int hL, int rL, V& Fc, V& Fd) {
-        const Q* A0 = sA + (z & 3) * HP;
-        const Q* AM = sA + ((z - 1) & 3) * HP;
-        const Q* AP = sA + ((z + 1) & 3) * HP;
-        const Q* B0 = sB + (z & 3) * HP;
-        const Q* BM = sB + ((z - 1) & 3) * HP;
-        const Q* BP = sB + ((z + 1) & 3) * HP;
-        const Q* C0 = sC + slot3(z) * HP;
-        const V* D0 = sD + (z & 1) * RP;
+    auto xface = [&](int am, int a0, int ap, int c0, int d0, int hL, int rL, V& Fc, V& Fd) {
+        const Q* A0 = sA + a0;
+        const Q* AM = sA + am;
+        const Q* AP = sA + ap;
+        const Q* B0 = sB + a0;
+        const Q* BM = sB + am;
+        const Q* BP = sB + ap;
+        const Q* C0 = sC + c0;
+        const V* D0 = sD + d0;
         const int hR = hL + 1;
         xface_core(A0[hL], B0[hL], A0[hR], B0[hR], A0[hL - HX], B0[hL - HX], A0[hR - HX], B0[hR - HX], A0[hL + HX],
                    B0[hL + HX], A0[hR + HX], B0[hR + HX], AP[hL], BP[hL], AP[hR], BP[hR], AM[hL], BM[hL], AM[hR],
                    BM[hR], C0[hL], C0[hR], D0[rL], D0[rL + 1], Fc, Fd);
     };
-    auto yface = [&](int z, int hL, int rL, V& Fc, V& Fd) {
-        const Q* A0 = sA + (z & 3) * HP;
-        const Q* AM = sA + ((z - 1) & 3) * HP;
-        const Q* AP = sA + ((z + 1) & 3) * HP;
-        const Q* B0 = sB + (z & 3) * HP;
-        const Q* BM = sB + ((z - 1) & 3) * HP;
-        const Q* BP = sB + ((z + 1) & 3) * HP;
-        const Q* C0 = sC + slot3(z) * HP;
-        const V* D0 = sD + (z & 1) * RP;
+    auto yface = [&](int am, int a0, int ap, int c0, int d0, int hL, int rL, V& Fc, V& Fd) {
+        const Q* A0 = sA + a0;
+        const Q* AM = sA + am;
+        const Q* AP = sA + ap;
+        const Q* B0 = sB + a0;
+        const Q* BM = sB + am;
+        const Q* BP = sB + ap;
+        const Q* C0 = sC + c0;
+        const V* D0 = sD + d0;
         const int hN = hL + HX;
         yface_core(A0[hL], B0[hL], A0[hN], B0[hN], A0[hL + 1], B0[hL + 1], A0[hL - 1], B0[hL - 1], A0[hN + 1],
                    B0[hN + 1], A0[hN - 1], B0[hN - 1], AP[hL], BP[hL], AM[hL], BM[hL], AP[hN], BP[hN], AM[hN],
@@ -414,17 +422,17 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     };
     // the own pair's x, y and z faces on plane z: 32 records of {phi, Y} and
     // {mu_s, mu_l}, 4 of {c_s, c_l} and 4 rates, each read once
-    auto own_faces = [&](int z, const V rate_here, const V rate_up, V& phi_here, V& Fxc, V& Fxd, V& Fyc, V& Fyd,
-                         V& Fzc, V& Fzd) {
+    auto own_faces = [&](int am, int a0, int ap, int c0, int c1, int d0, const V rate_here, const V rate_up,
+                         V& phi_here, V& Fxc, V& Fxd, V& Fyc, V& Fyd, V& Fzc, V& Fzd) {
         const int h = own_h, r = own_r;
-        const Q* A0 = sA + (z & 3) * HP;
-        const Q* AM = sA + ((z - 1) & 3) * HP;
-        const Q* AP = sA + ((z + 1) & 3) * HP;
-        const Q* B0 = sB + (z & 3) * HP;
-        const Q* BM = sB + ((z - 1) & 3) * HP;
-        const Q* BP = sB + ((z + 1) & 3) * HP;
-        const Q* C0 = sC + slot3(z) * HP;
-        const V* D0 = sD + (z & 1) * RP;
+        const Q* A0 = sA + a0;
+        const Q* AM = sA + am;
+        const Q* AP = sA + ap;
+        const Q* B0 = sB + a0;
+        const Q* BM = sB + am;
+        const Q* BP = sB + ap;
+        const Q* C0 = sC + c0;
+        const V* D0 = sD + d0;
         // plane z: the pair O, its x neighbours E, W, the pairs N, S and NE, SE, NW
         const Q aO = A0[h], bO = B0[h], aE = A0[h + 1], bE = B0[h + 1], aW = A0[h - 1], bW = B0[h - 1];
         const Q aN = A0[h + HX], bN = B0[h + HX], aS = A0[h - HX], bS = B0[h - HX];
@@ -440,7 +448,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         yface_core(aO, bO, aN, bN, aE, bE, aW, bW, aNE, bNE, A0[h + HX - 1], B0[h + HX - 1], aU, bU, aD, bD, aUN,
                    bUN, AM[h + HX], BM[h + HX], cO, C0[h + HX], dO, D0[r + RX], Fyc, Fyd);
         zface_core(aO, bO, aU, bU, aE, bE, aW, bW, aUE, bUE, AP[h - 1], BP[h - 1], aS, bS, AP[h - HX], BP[h - HX],
-                   aN, bN, aUN, bUN, cO, sC[slot3(z + 1) * HP + h], dO, rate_up, Fzc, Fzd);
+                   aN, bN, aUN, bUN, cO, sC[c1 + h], dO, rate_up, Fzc, Fzd);
     };
     auto z_noflux = [&](int z) {
         return (z == -1 && G.bc_lo[2] == BC_NOFLUX) || (z == nz - 1 && G.bc_hi[2] == BC_NOFLUX);
@@ -457,7 +465,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         fetch_plane(z);
         cp_async_commit();
         cp_async_wait_all();
-        store_plane(z);
+        store_plane(offA(z), offC(z));
         __syncthreads();
     }
     rates_plane(z0 - 1);
@@ -465,7 +473,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();   // plane z0+1 reuses the {c_s, c_l} / phi slots of z0-2
-    store_plane(z0 + 1);
+    store_plane(offA(z0 + 1), offC(z0 + 1));
     __syncthreads();
     rates_plane(z0);
     fetch_plane(z0 + 2);
@@ -482,6 +490,13 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     // faced, read by the z face of k and by the update of k)
     V rate_k = sD[(z0 & 1) * RP + own_r], rate_prev = fxc, phi_prev = fxc;
     // update of plane k from its fluxes and the own-cell state staged in sO
+    // ring offsets of the planes an iteration k touches, rotated per plane:
+    // A/B rings k-1 .. k+2, C/P rings k .. k+2, rates k, k+1
+    int ra_m1 = offA(z0 - 1), ra_0 = offA(z0), ra_p1 = offA(z0 + 1), ra_p2 = offA(z0 + 2);
+    int rc_0 = offC(z0), rc_p1 = offC(z0 + 1), rc_p2 = offC(z0 + 2);
+    int rd_0 = offD(z0), rd_p1 = offD(z0 + 1);
+    // update of plane k: its rate and phi sit at D offset rd_p1 and A offset
+    // ra_m1 whenever it runs (inside iteration k+1, and after the loop)
     auto update = [&](int k) {
         const Q left = sFx[ty * FXP + tx];
         const V below = sFy[ty * TX + tx];
@@ -491,11 +506,11 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V c_k = vpair(sO[tid], sO[NT + tid]), d_k = vpair(sO[2 * NT + tid], sO[3 * NT + tid]);
         V phi_new;
         if constexpr (sizeof(T) == 4) phi_new = vfma(K.dt_dx2, rate_prev, phi_prev);
-        else phi_new = vfma(K.dt_dx2, sD[(k & 1) * RP + own_r], sA[(k & 3) * HP + own_h].a);
+        else phi_new = vfma(K.dt_dx2, sD[rd_p1 + own_r], sA[ra_m1 + own_h].a);
         const V d_new = vfma(K.dt_dx2, dFd, d_k);
         const V dcv = vmul(K.dt_dx2, dFc);
         V c_new, lo_new;
-        if (clo_in != nullptr) {
+        if constexpr (sizeof(T) == 4) {
             // compensated (TwoSum) update of c = hi + lo
             const V lo_k = vpair(sO[4 * NT + tid], sO[5 * NT + tid]);
             const V s_ = vadd(c_k, dcv);
@@ -513,13 +528,13 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             phi_out[gi] = phi_new.x;
             c_out[gi] = c_new.x;
             d_out[gi] = d_new.x;
-            if (clo_out != nullptr) clo_out[gi] = lo_new.x;
+            if constexpr (sizeof(T) == 4) clo_out[gi] = lo_new.x;
         }
         if (in_hi) {
             phi_out[gi + nx] = phi_new.y;
             c_out[gi + nx] = c_new.y;
             d_out[gi + nx] = d_new.y;
-            if (clo_out != nullptr) clo_out[gi + nx] = lo_new.y;
+            if constexpr (sizeof(T) == 4) clo_out[gi + nx] = lo_new.y;
         }
         fzc_down = fzc;
         fzd_down = fzd;
@@ -532,27 +547,31 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     for (int k = z0; k < z1; ++k) {
         cp_async_wait_all();
         if (k > z0) update(k - 1);
-        store_plane(k + 2);
+        store_plane(ra_p2, rc_p2);
         __syncthreads();
         if (k + 1 < z1) fetch_plane(k + 3);
         fetch_own(k);
         cp_async_commit();
+        const bool ghost_up = ghost(k + 1);
         if constexpr (sizeof(T) == 4) {
             // The own rate of plane k+1 goes to the z face in a register and to
             // shared memory only after the faces: with no shared store between
             // them, the records the rate and the faces both read are read once.
-            const V rate_up = rate_of(k + 1, own_dsc, own_xc);
+            const V rate_up = rate_of(ghost_up, ra_0, ra_p1, ra_p2, rc_0, rc_p1, rc_p2, own_dsc, own_xc);
             V phi_k;
-            own_faces(k, rate_k, rate_up, phi_k, fxc, fxd, fyc, fyd, fzc, fzd);
-            sD[((k + 1) & 1) * RP + own_r] = rate_up;
-            if (bor_r >= 0) rate_cell(k + 1, bor_dsc, bor_xc, bor_r);
+            own_faces(ra_m1, ra_0, ra_p1, rc_0, rc_p1, rd_0, rate_k, rate_up, phi_k, fxc, fxd, fyc, fyd, fzc, fzd);
+            sD[rd_p1 + own_r] = rate_up;
+            if (bor_r >= 0)
+                sD[rd_p1 + bor_r] = rate_of(ghost_up, ra_0, ra_p1, ra_p2, rc_0, rc_p1, rc_p2, bor_dsc, bor_xc);
             rate_prev = rate_k;
             phi_prev = phi_k;
             rate_k = rate_up;
         } else {   // FP64: one face at a time keeps fewer registers live
-            rates_plane(k + 1);
-            xface(k, own_h, own_r, fxc, fxd);
-            yface(k, own_h, own_r, fyc, fyd);
+            sD[rd_p1 + own_r] = rate_of(ghost_up, ra_0, ra_p1, ra_p2, rc_0, rc_p1, rc_p2, own_dsc, own_xc);
+            if (bor_r >= 0)
+                sD[rd_p1 + bor_r] = rate_of(ghost_up, ra_0, ra_p1, ra_p2, rc_0, rc_p1, rc_p2, bor_dsc, bor_xc);
+            xface(ra_m1, ra_0, ra_p1, rc_0, rd_0, own_h, own_r, fxc, fxd);
+            yface(ra_m1, ra_0, ra_p1, rc_0, rd_0, own_h, own_r, fyc, fyd);
             zface(k, own_h, own_r, fzc, fzd);
         }
         if (nf_x) fxc = fxd = vpair(T(0), T(0));
@@ -564,17 +583,24 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         if (tid < TYP) {
             // x faces on the tile's low x edge, pair row tid
             V ec, ed;
-            xface(k, (tid + 1) * HX + 1, (tid + 1) * RX, ec, ed);
+            xface(ra_m1, ra_0, ra_p1, rc_0, rd_0, (tid + 1) * HX + 1, (tid + 1) * RX, ec, ed);
             if (nf_x_edge) ec = ed = vpair(T(0), T(0));
             sFx[tid * FXP] = Q{ec, ed};
         } else if (tid >= 32 && tid < 32 + TX) {
             // y face on the tile's low y edge (upper lane of the pair row below the tile)
             const int ex = tid - 32;
             V ec, ed;
-            yface(k, ex + 2, ex + 1, ec, ed);
+            yface(ra_m1, ra_0, ra_p1, rc_0, rd_0, ex + 2, ex + 1, ec, ed);
             sFy[ex] = nf_y_edge ? vpair(T(0), T(0)) : vpair(ec.y, ed.y);
         }
         __syncthreads();
+        // rotate the ring offsets to iteration k+1
+        const int ta = ra_m1;
+        ra_m1 = ra_0; ra_0 = ra_p1; ra_p1 = ra_p2; ra_p2 = ta;
+        const int tc = rc_0;
+        rc_0 = rc_p1; rc_p1 = rc_p2; rc_p2 = tc;
+        const int td = rd_0;
+        rd_0 = rd_p1; rd_p1 = td;
     }
     cp_async_wait_all();
     update(z1 - 1);
