@@ -72,12 +72,12 @@ FP32_LANES, MUFU_LANES = 128, 16    # per SM and clock: FP32 FMA lanes, MUFU res
 # of the kernel's device code the capture ran.  The figure is reported as null
 # as soon as those sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.543744e6 + 228.566016e6) / 256 ** 3,
+    "bytes_per_cell_update": (280.333824e6 + 229.011456e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh"),
-    "sha256": ("bcc4cc8026c96a54a566476cd9b6003b19d081729202abd224acc16eced012e3",
+    "sha256": ("0ba62320a52a7cef948cada821d5df79d7c31c95ea5c48deb413111a781b42d7",
                "ca8a8936b55cf3a8d7bbbc6ef71bd5cec65b4f4c0f6931f1105397cc5e2714b8",
-               "6bcc452ab68864856fed32a5d80fcb6a87e6984d7a9316d9bf24f30de572ec60"),
+               "47c14bc813e01ef31966d105fe81a4bca92110885cc77bf8470a1be24dce418c"),
 }
 
 
@@ -391,6 +391,57 @@ def run_slabs(args, torch, dist, world, rank, local):
     return 0
 
 
+def run_banding(args):
+    """The band-forming workload of Sec. "Oscillations and solute bands": Si-As
+    pulled fronts at G = 1.4e6 K/m and D_s/D_l = 1e-3 (banding_front), pulled
+    at 0.1, 0.2, 0.3 and 0.5 m/s, 8192 cells each (4096 W), FP32, through the
+    batched kernel for `--steps` steps (default 2x10^5 = 2x10^4 time units),
+    at the two trapping settings that stay finite from this start (A = 1, b = 1
+    and A = 1.5, b = 0.1; the paper's own A = 2, b = 1e-3 diverges).  Reports
+    cell-updates/s and, per front, the final k_v and the front's offset from
+    the pulled reference position; oscillating fronts would show up as
+    unsettled offsets and k_v between partitioning and trapping."""
+    from paper_2303_09671_gb300 import pf
+    K = args.steps if args.steps != 2000 else 200000
+    vps = [0.1, 0.2, 0.3, 0.5]
+    n = 8192
+    out = {"metric": "phi/c_s/c_l cell-updates/s (banding: Si-As pulled fronts, batched)", "unit": "cell-updates/s",
+           "n_gpus": 1, "steps": K, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "Si-As, G=1.4e6 K/m, D_s/D_l=1e-3, v_p 0.1..0.5 m/s, W=d0, 8192 cells, "
+                                  "start at the liquidus of c_inf"}, "runs": []}
+    total_cells, total_s = 0, 0.0
+    for A, b in ((1.0, 1.0), (1.5, 0.1)):
+        made = [wl.banding_front(v, A=A, b=b, N=n) for v in vps]
+        prs = [m[0] for m in made]
+        vs = [pr["v_pull"] for pr in prs]
+        dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+        f32 = [np.concatenate([m[i] for m in made]).astype(np.float32) for i in (1, 2, 3)]
+        spl = 5000
+        pf.run_batch(prs[0], [n] * 4, vs, *f32, dt=dts, max_steps=spl, steps_per_launch=spl,
+                     launches_per_graph=1, tol=-1.0)                                   # warm-up
+        res = pf.run_batch(prs[0], [n] * 4, vs, *f32, dt=dts, max_steps=K, steps_per_launch=spl,
+                           launches_per_graph=4, check_every=K, tol=-1.0, want_fields=True)
+        total_cells += 4 * n * K
+        total_s += res["gpu_ms"] * 1e-3
+        for i, (pr, v, dt) in enumerate(zip(prs, vs, dts)):
+            f = res["phi"][i * n:(i + 1) * n].astype(np.float64)
+            j = np.where((f[:-1] >= 0.5) & (f[1:] < 0.5))[0]
+            t = float(res["t"][i])
+            shifts = int(np.floor(v * t / pr["dx"]))
+            if len(j):
+                a_, b_ = f[j[-1]], f[j[-1] + 1]
+                xw = (j[-1] + 0.5 + (a_ - 0.5) / (a_ - b_)) * pr["dx"]
+                offset = xw + shifts * pr["dx"] - pr["x0"] - v * t
+            else:
+                offset = None
+            out["runs"].append({"A": A, "b": b, "v_p_m_s": vps[i], "V": v, "t": t, "k_v": float(res["k_v"][i]),
+                                "front_minus_pulled_W": offset, "crossings": int(len(j))})
+    out["value"] = total_cells / total_s
+    out["gpu_s"] = total_s
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -666,7 +717,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="leave out the bounded kv_sweep and adjoint keys of the default line")
     ap.add_argument("--workload", default="sphere3d",
-                    choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d"])
+                    choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d", "banding"])
     ap.add_argument("--mode", default="slabs", choices=["slabs", "replicas"],
                     help="N > 1: one grid cut into z-slabs with a halo exchange every step (strong "
                          "scaling), or one independent grid per rank (weak scaling)")
@@ -678,6 +729,8 @@ def main():
         return run_adjoint(args)
     if args.workload in ("planar1d", "perturbed2d"):
         return run_secondary(args)
+    if args.workload == "banding":
+        return run_banding(args)
     if args.impl == "reference":
         return run_reference(args)
 

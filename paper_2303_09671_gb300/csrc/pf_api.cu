@@ -407,12 +407,18 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
     void* out[3] = {phi, cs, cl};
     const pf::Fields& st = h->buf[h->cur ^ 1];
     void* tgt[3] = {phi, cs, cl};
-    if (where == PF_HOST) {
+    // page-locked host memory is written by the conversion kernel itself;
+    // other host memory through a device staging copy
+    const void* views[3] = {phi, cs, cl};
+    const bool mapped = where == PF_HOST && device_views(views);
+    if (mapped) {
+        for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
+    } else if (where == PF_HOST) {
         tgt[0] = st.phi; tgt[1] = st.c; tgt[2] = st.d;
     }
     cudaError_t e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
-    if (where == PF_HOST) {
+    if (where == PF_HOST && !mapped) {
         for (int f = 0; f < 3; ++f) {
             e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");

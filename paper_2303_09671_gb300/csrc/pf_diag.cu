@@ -429,6 +429,57 @@ __global__ void from_state_kernel(StateView<T> S, long long n, DiagConsts C, T* 
     }
 }
 
+// FP32 state -> (phi, c_s, c_l) in FP32 arithmetic: p(phi) in FP32, then
+// c_s = c_hi + fma(1 - p, d, c_lo), c_l = c_hi + fma(-p, d, c_lo), so that the
+// low word of c enters before the one rounding of each result
+__device__ __forceinline__ void from_f32(float f, float hi, float lo, float d, float a, bool cubic, float& s,
+                                         float& l) {
+    const float g = f * (1.0f - f);
+    const float h = cubic ? f * f * (3.0f - 2.0f * f) : f * f * f * (f * (6.0f * f - 15.0f) + 10.0f);
+    const float p = h + a * (f - 0.5f) * g * g;
+    s = hi + fmaf(1.0f - p, d, lo);
+    l = hi + fmaf(-p, d, lo);
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+from_state_f32_kernel(const float* __restrict__ phi, const float* __restrict__ c, const float* __restrict__ clo,
+                      const float* __restrict__ d, long long n, DiagConsts C, float* __restrict__ po,
+                      float* __restrict__ cs, float* __restrict__ cl) {
+    const float a = (float)C.a;
+    const bool cubic = C.interp == 1;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s, l;
+        from_f32(phi[i], c[i], clo[i], d[i], a, cubic, s, l);
+        po[i] = phi[i];
+        cs[i] = s;
+        cl[i] = l;
+    }
+}
+
+// the same, 4 cells per thread and iteration with 16-byte accesses (every
+// array 16-byte aligned): the read-back to page-locked host memory is bound by
+// the host link, and wide requests keep more bytes in flight per thread
+__global__ void __launch_bounds__(DIAG_THREADS)
+from_state_f32x4_kernel(const float4* __restrict__ phi, const float4* __restrict__ c,
+                        const float4* __restrict__ clo, const float4* __restrict__ d, long long n4, DiagConsts C,
+                        float4* __restrict__ po, float4* __restrict__ cs, float4* __restrict__ cl) {
+    const float a = (float)C.a;
+    const bool cubic = C.interp == 1;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 f = phi[i], h = c[i], lo = clo[i], dd = d[i];
+        float4 s, l;
+        from_f32(f.x, h.x, lo.x, dd.x, a, cubic, s.x, l.x);
+        from_f32(f.y, h.y, lo.y, dd.y, a, cubic, s.y, l.y);
+        from_f32(f.z, h.z, lo.z, dd.z, a, cubic, s.z, l.z);
+        from_f32(f.w, h.w, lo.w, dd.w, a, cubic, s.w, l.w);
+        po[i] = f;
+        cs[i] = s;
+        cl[i] = l;
+    }
+}
+
 static DiagConsts make_diag(const HostProblem& P, int64_t step, int64_t shifts) {
     DiagConsts C;
     for (int a = 0; a < 3; ++a) {
@@ -564,12 +615,32 @@ cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi,
                               cudaStream_t s) {
     const DiagConsts C = make_diag(P, 0, 0);
     const long long n = P.cells();
-    if (P.precision == 1)
+    if (P.precision == 1) {
         from_state_kernel<double><<<diag_grid(), DIAG_THREADS, 0, s>>>(
             view<double>(in), n, C, (double*)phi, (double*)cs, (double*)cl);
-    else
+        return cudaGetLastError();
+    }
+    if (in.clo == nullptr) {   // no low word of c (not a state of this library's FP32 handles)
         from_state_kernel<float><<<diag_grid(), DIAG_THREADS, 0, s>>>(
             view<float>(in), n, C, (float*)phi, (float*)cs, (float*)cl);
+        return cudaGetLastError();
+    }
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const float *f = (const float*)in.phi, *c = (const float*)in.c, *lo = (const float*)in.clo,
+                *d = (const float*)in.d;
+    long long n4 = 0;
+    if (al(f) && al(c) && al(lo) && al(d) && al(phi) && al(cs) && al(cl)) {
+        n4 = n / 4;
+        if (n4 > 0)
+            from_state_f32x4_kernel<<<diag_grid(), DIAG_THREADS, 0, s>>>(
+                (const float4*)f, (const float4*)c, (const float4*)lo, (const float4*)d, n4, C, (float4*)phi,
+                (float4*)cs, (float4*)cl);
+    }
+    const long long o = 4 * n4;
+    if (o < n)
+        from_state_f32_kernel<<<diag_grid(), DIAG_THREADS, 0, s>>>(f + o, c + o, lo + o, d + o, n - o, C,
+                                                                   (float*)phi + o, (float*)cs + o,
+                                                                   (float*)cl + o);
     return cudaGetLastError();
 }
 

@@ -449,11 +449,15 @@ def adjoint(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, *, k_target=None,
 
 def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, iters=50, lr=0.05,
               wrt=("M_phi", "A", "b"), precision="fp32", dt=None, betas=(0.9, 0.999), eps=1e-8,
-              callback=None, mode="tangent"):
+              callback=None, mode="tangent", bounds=None):
     """Adam on the logarithms of the chosen parameters (M_phi, A, b > 0), each
-    iteration one pf_adjoint run; returns (parameters, history of losses)."""
+    iteration one pf_adjoint run; returns (parameters, history of losses).
+    bounds: optional {name: (lo, hi)}; a parameter is clamped into its range
+    after every update (the model diverges for some parameter sets)."""
     idx = [ADJ_PARAMS.index(w) for w in wrt]
     theta = np.log(np.array([pr[ADJ_PARAMS[j]] for j in idx], dtype=np.float64))
+    lo = np.array([np.log((bounds or {}).get(ADJ_PARAMS[j], (0.0, np.inf))[0] or 1e-300) for j in idx])
+    hi = np.array([np.log((bounds or {}).get(ADJ_PARAMS[j], (0.0, np.inf))[1]) for j in idx])
     m = np.zeros_like(theta)
     v = np.zeros_like(theta)
     hist = []
@@ -469,7 +473,7 @@ def calibrate(pr: dict, lengths, v_pull, phi0, cs0, cl0, nsteps, k_target, *, it
         v = betas[1] * v + (1 - betas[1]) * g * g
         mh = m / (1 - betas[0] ** it)
         vh = v / (1 - betas[1] ** it)
-        theta = theta - lr * mh / (np.sqrt(vh) + eps)
+        theta = np.clip(theta - lr * mh / (np.sqrt(vh) + eps), lo, hi)
         if callback is not None:
             callback(it, cur, r)
     for j, t in zip(idx, theta):

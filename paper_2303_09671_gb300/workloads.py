@@ -308,3 +308,17 @@ def physical_pulled_front(alloy, v_p, G, Ds_ratio, *, N=2048, dx=0.5, W=None, fr
     pr["units"] = u
     return pr, phi, cs, cl
 
+
+
+def banding_front(v_p=0.3, *, A=1.0, b=1.0, N=8192, dx=0.5, front_cell=6000, theta_start=1.0, **kw):
+    """A pulled Si-As front at the parameters of the paper's solute-band run
+    (Sec. "Oscillations and solute bands": G = 1.4e6 K/m, D_s/D_l = 1e-3,
+    v_p = 0.3 m/s; W = d_0), converted to scaled units by physical_pulled_front.
+    The interface starts at theta = theta_start (the liquidus of c_inf at 1.0)
+    instead of the solidus of c_inf, and far from the cold end of the window,
+    so that the front reaches its steady position inside the window: the
+    gradient of 5.25e-4 per W is too shallow for the solidus start."""
+    pr, phi, cs, cl = physical_pulled_front("Si-As", v_p, 1.4e6, 1e-3, N=N, dx=dx, front_cell=front_cell,
+                                            A=A, b=b, **kw)
+    pr["theta_ref"] = float(theta_start)
+    return pr, phi, cs, cl

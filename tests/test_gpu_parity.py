@@ -483,3 +483,27 @@ def test_step_energies_match_per_call_energies(precision, case):
         assert a.clock == b.clock
         if case == "planar1d":
             assert np.all(np.diff(Fa) <= 1e-12 * abs(Fa[0]))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_get_fields_to_pinned_host_memory(precision):
+    """pf_get_fields writes page-locked host memory from the conversion kernel
+    itself; the fields equal those staged through device memory into pageable
+    host memory and those copied to device tensors, bit for bit (in FP32 the
+    conversion runs in FP32 arithmetic, c_s = c_hi + fma(1 - p, d, c_lo),
+    c_l = c_hi + fma(-p, d, c_lo); the FP32 parity tests hold its results to
+    the oracle)."""
+    torch = pytest.importorskip("torch")
+    pr, phi, cs, cl = wl.random_state(3, (48, 19, 13), dx=0.5, A=1.5, b=0.3, seed=17)
+    dt = np.float64 if precision == "fp64" else np.float32
+    with Sim(pr, precision) as s:
+        s.set_fields(*(np.asarray(a, dtype=dt) for a in (phi, cs, cl)))
+        s.step(3)
+        pageable = s.get_fields()
+        pinned = [torch.empty(a.shape, dtype=torch.float64 if precision == "fp64" else torch.float32).pin_memory()
+                  for a in pageable]
+        s.get_fields(out_host=[p.numpy() for p in pinned])
+        dev = [torch.empty(a.shape, dtype=pinned[0].dtype, device="cuda") for a in pageable]
+        s.get_fields(out=dev)
+    for a, b, c in zip(pageable, pinned, dev):
+        assert np.array_equal(a, b.numpy()) and np.array_equal(a, c.cpu().numpy())
