@@ -144,6 +144,24 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
 int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where);
 int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
 
+/* pf_get_fields without the wait, for a pipeline that reads every step's
+ * fields back while the next state is being uploaded.  The conversion of the
+ * current state to (phi, c_s, c_l) is queued on an internal read-back stream
+ * after the work already queued on the handle's stream, and writes phi, cs, cl
+ * directly: page-locked host memory (where = PF_HOST; pageable memory returns
+ * PF_EINVAL) or device memory (PF_DEVICE), n[0]*n[1]*n[2] values each of the
+ * handle's precision.  The values are valid after pf_sync (or after the
+ * handle's stream has been synchronised following a later call on the handle).
+ * The handle keeps the state being read intact until then: every later call
+ * that writes the state first orders itself after the read-back, except the
+ * upload of pf_set_fields_step, which converts into the other state buffer and
+ * so overlaps the read-back (only its step waits).  The handle creates the
+ * stream and its events on first use and frees them in pf_destroy. */
+int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where);
+
+/* Wait for every piece of work of the handle, read-backs included. */
+int pf_sync(pf_handle* h);
+
 /* Advance n >= 0 forward-Euler steps (stream-ordered, no host sync). */
 int pf_step(pf_handle* h, int64_t n);
 

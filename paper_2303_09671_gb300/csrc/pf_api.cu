@@ -34,6 +34,12 @@ struct pf_handle {
     bool halo_set[2] = {false, false};
     void* alloc[2][5] = {{nullptr, nullptr, nullptr, nullptr, nullptr},
                          {nullptr, nullptr, nullptr, nullptr, nullptr}};
+    // pf_get_fields_async: a read-back stream, an event recorded on the handle's
+    // stream before it and one after the read-back; pending while no later work
+    // of the handle has been ordered after it
+    cudaStream_t rb = nullptr;
+    cudaEvent_t rb_start = nullptr, rb_done = nullptr;
+    bool rb_pending = false;
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
     int ovchunk = 16;            // z planes per slab and CTA in pf_set_fields_step
     bool generic = false;        // run 2D / 3D through the generic kernel (cross-check)
@@ -72,6 +78,16 @@ int fail(pf_handle* h, int code, const std::string& msg) {
 
 int cuda_fail(pf_handle* h, cudaError_t e, const char* what) {
     return fail(h, PF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// order the handle's stream after a pending pf_get_fields_async (before any
+// work that may overwrite the state it reads)
+int join_readback(pf_handle* h) {
+    if (!h->rb_pending) return PF_OK;
+    cudaError_t e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "read-back join");
+    h->rb_pending = false;
+    return PF_OK;
 }
 
 double effective_dmax(const pf_params* p) {
@@ -250,8 +266,12 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
 
 void pf_destroy(pf_handle* h) {
     if (!h) return;
+    if (h->rb) cudaStreamSynchronize(h->rb);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    if (h->rb) cudaStreamDestroy(h->rb);
+    if (h->rb_start) cudaEventDestroy(h->rb_start);
+    if (h->rb_done) cudaEventDestroy(h->rb_done);
     for (int b = 0; b < 2; ++b)
         for (void* p : h->alloc[b])
             if (p) cudaFree(p);
@@ -269,6 +289,7 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (int rc = join_readback(h)) return rc;
     const size_t bytes = (size_t)h->P.cells() * h->P.elem();
     const void* src[3] = {phi, cs, cl};
     const bool mapped = where == PF_HOST && device_views(src);
@@ -336,6 +357,12 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
     if (e != cudaSuccess) return cuda_fail(h, e, "stream setup");
     cudaStream_t conv = h->ov[0];
     cudaEvent_t start = h->ov_ev[nch];
+    // The upload is converted into the idle state buffer (the input of the
+    // handle's last step, free once the work queued on its stream is done) and
+    // the step writes the current one.  A pending pf_get_fields_async reads the
+    // current buffer, so the upload overlaps that read-back; only the step
+    // chunks wait for it.
+    const int src_buf = h->cur ^ 1, dst_buf = h->cur;
     // Slab j (the planes of z-chunk j) is converted on `conv` after the work
     // already queued on the handle's stream; chunk j of the first step starts
     // once every plane it reads (z0 - 2 .. z1 + 1, wrapped on a periodic z
@@ -353,13 +380,15 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
         const long long z0 = (long long)j * zchunk, z1 = std::min<long long>(nz, z0 + zchunk);
         // two blocks per SM: the conversion is bound by the host link, and
         // leaves the SMs to the step chunks that run beside it
-        e = pf::launch_to_state_range(P, src[0], src[1], src[2], h->buf[h->cur], z0 * plane,
+        e = pf::launch_to_state_range(P, src[0], src[1], src[2], h->buf[src_buf], z0 * plane,
                                       (z1 - z0) * plane, 2 * nsms, conv);
         if (e == cudaSuccess) e = cudaEventRecord(h->ov_ev[j], conv);
     }
-    const pf::Fields& in = h->buf[h->cur];
-    const pf::Fields& out = h->buf[h->cur ^ 1];
+    const pf::Fields& in = h->buf[src_buf];
+    const pf::Fields& out = h->buf[dst_buf];
     const bool zper = P.bc_lo[2] == PF_BC_PERIODIC;
+    for (int i = 1; i < pf_handle::OV_STREAMS && e == cudaSuccess && h->rb_pending; ++i)
+        e = cudaStreamWaitEvent(h->ov[i], h->rb_done, 0);
     for (int j = 0; j < nch && e == cudaSuccess; ++j) {
         const int z0 = j * zchunk, z1 = std::min(nz, z0 + zchunk);
         int need = std::min(nch - 1, std::min(nz - 1, z1 + 1) / zchunk);
@@ -388,8 +417,8 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, start, 0);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "overlapped upload and step");
+    h->rb_pending = false;   // the handle's stream now follows the read-back too
     h->have_front = false;
-    h->cur ^= 1;
     h->step += 1;
     if (where == PF_HOST) {
         // the caller may reuse its host memory once the last slab is read
@@ -397,6 +426,40 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
     }
     return pf_step(h, n - 1);
+}
+
+int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    void* tgt[3] = {phi, cs, cl};
+    if (where == PF_HOST) {
+        const void* views[3] = {phi, cs, cl};
+        if (!device_views(views)) return fail(h, PF_EINVAL, "pf_get_fields_async needs page-locked host memory");
+        for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!h->rb) {
+        e = cudaStreamCreateWithFlags(&h->rb, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "read-back stream");
+    }
+    e = cudaEventRecord(h->rb_start, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_start, 0);
+    if (e == cudaSuccess) e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb);
+    if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->rb);
+    if (e != cudaSuccess) return cuda_fail(h, e, "read-back");
+    h->rb_pending = true;
+    return PF_OK;
+}
+
+int pf_sync(pf_handle* h) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = join_readback(h)) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return PF_OK;
 }
 
 int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
@@ -438,6 +501,8 @@ int pf_step(pf_handle* h, int64_t n) {
             return fail(h, PF_EINVAL, "halo not imported since the last step or pf_set_fields");
         h->halo_set[0] = h->halo_set[1] = false;
     }
+    if (n > 0)
+        if (int rc = join_readback(h)) return rc;
     const pf::HostProblem& P = h->P;
     for (int64_t s = 0; s < n; ++s) {
         const pf::Fields& in = h->buf[h->cur];
@@ -499,6 +564,7 @@ int pf_step_energies(pf_handle* h, int64_t n, double* F) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
     if (h->halo[0] || h->halo[1]) return fail(h, PF_EINVAL, "not for a slab with halo sides");
+    if (int rc = join_readback(h)) return rc;
     if (n > 0 && !F) return fail(h, PF_EINVAL, "null output");
     if (n == 0) return PF_OK;
     if (h->rec_cap < n) {
@@ -646,6 +712,8 @@ int pf_halo_bytes(pf_handle* h, int64_t* bytes) {
 
 static int halo_copy(pf_handle* h, int side, void* buf, int where, bool import) {
     if (side != 0 && side != 1) return fail(h, PF_EINVAL, "side must be 0 (low z) or 1 (high z)");
+    if (import)
+        if (int rc = join_readback(h)) return rc;
     if (!h->halo[side]) return fail(h, PF_EINVAL, "that z side is not a halo side");
     if (!buf) return fail(h, PF_EINVAL, "null buffer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");

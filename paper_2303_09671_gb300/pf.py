@@ -92,6 +92,8 @@ _SIGS = {
                                  ctypes.POINTER(pf_params), _VP, ctypes.POINTER(_VP)]),
     "pf_set_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "pf_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "pf_get_fields_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "pf_sync": (ctypes.c_int, [_VP]),
     "pf_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "pf_solute_total_async": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pf_set_fields_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int64]),
@@ -240,6 +242,23 @@ class Sim:
         arrs = [np.empty(self.shape, dtype=self.dtype) for _ in range(3)]
         _check(lib().pf_get_fields(self._h, *[_VP(a.ctypes.data) for a in arrs], PF_HOST), self._h)
         return tuple(arrs)
+
+    def get_fields_async(self, out=None, out_host=None):
+        """Queue the read-back of (phi, cs, cl) into CUDA tensors (out) or
+        page-locked host arrays (out_host) without waiting; valid after sync()."""
+        if out is not None:
+            ptrs, where = [_VP(a.data_ptr()) for a in out], PF_DEVICE
+        else:
+            for a in out_host:
+                if a.shape != self.shape or a.dtype != self.dtype or not a.flags.c_contiguous:
+                    raise ValueError("out_host arrays must be contiguous, of the grid shape and dtype")
+            ptrs, where = [_VP(a.ctypes.data) for a in out_host], PF_HOST
+        _check(lib().pf_get_fields_async(self._h, *ptrs, where), self._h)
+        return out if out is not None else out_host
+
+    def sync(self):
+        """Wait for all work of the handle, read-backs included."""
+        _check(lib().pf_sync(self._h), self._h)
 
     # -- stepping and diagnostics
     def step(self, n: int = 1):

@@ -1,7 +1,7 @@
 """The band-forming workload of Sec. "Oscillations and solute bands" (Si-As
 at G = 1.4e6 K/m, D_s/D_l = 1e-3, pulled at 0.1-0.5 m/s) through the batched
 pulled-front kernel, FP64 against the oracle: every field after 2x10^4 steps
-(2000 time units, thousands of window shifts) at the batch bar."""
+(2000 time units, 360 to 1800 window shifts) at the batch bar."""
 import numpy as np
 import pytest
 
@@ -30,7 +30,7 @@ def test_banding_fronts_fp64_match_oracle(A, b):
     for i, (pr, dt) in enumerate(zip(prs, dts)):
         st = oracle.State(dict(pr, dt=dt), *(a[i * n:(i + 1) * n] for a in (phi, cs, cl)))
         st.step(steps)
-        assert st.clock.shifts > 1000
+        assert st.clock.shifts == int(np.floor(pr["v_pull"] * steps * dt / pr["dx"])) >= 300
         g = [res[k][i * n:(i + 1) * n] for k in ("phi", "cs", "cl")]
         for a, o in zip(g, (st.phi, st.cs, st.cl)):
             assert rel_err(a, o) <= 1e-11, (vps[i], rel_err(a, o))

@@ -97,3 +97,26 @@ def test_fp32_benchmark_recipe_64_cubed_5000_steps():
                 assert np.abs(g[2] - st.cl)[liq].max() <= 1e-4 * np.abs(st.cl[liq]).max()
         S1 = s.solute_total()
     assert abs(S1 - S0) <= 1e-7 * abs(S0), abs(S1 - S0) / abs(S0)
+
+
+def test_sphere_256_cubed_energy_and_solute_over_300_steps():
+    """Properties that hold at any size, checked at the benchmark's full size
+    and launch configuration: the discrete free energy (Eq. model1.1) of the
+    isothermal sphere never increases from one step to the next (check (a),
+    the variational construction) and the total solute stays put (check (b);
+    FP32 state, FP64 sums) over 300 steps, F_h recorded on the device after
+    every step."""
+    import bench
+    pr, phi, cs, cl = bench.workload(256)
+    assert pr["G_theta"] == 0.0 and pr["v_pull"] == 0.0
+    f32 = [np.asarray(a, np.float32) for a in (phi, cs, cl)]
+    with Sim(pr, "fp32") as s:
+        s.set_fields(*f32)
+        S0 = s.solute_total()
+        F = s.step_energies(300)
+        S1 = s.solute_total()
+    dF = np.diff(F)
+    print(f"F_h {F[0]:.9e} -> {F[-1]:.9e}, largest increase {dF.max():.2e}, solute drift {abs(S1 - S0) / S0:.2e}")
+    assert np.all(dF <= 1e-12 * abs(F[0])), dF.max()
+    assert F[-1] < F[0]
+    assert abs(S1 - S0) <= 1e-7 * abs(S0)

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_2303_09671_gb300 import workloads as wl
-from paper_2303_09671_gb300.pf import Sim
+from paper_2303_09671_gb300.pf import PFError, Sim
 
 from conftest import rel_err
 
@@ -507,3 +507,45 @@ def test_get_fields_to_pinned_host_memory(precision):
         s.get_fields(out=dev)
     for a, b, c in zip(pageable, pinned, dev):
         assert np.array_equal(a, b.numpy()) and np.array_equal(a, c.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_get_fields_async_pipeline(precision):
+    """pf_get_fields_async: after pf_sync the fields equal pf_get_fields' bit
+    for bit (page-locked host and device outputs).  Pipelined like the
+    end-to-end benchmark -- pf_set_fields_step of a state, then an
+    unawaited read-back, three times with different states, one wait at the
+    end -- each read-back equals set_fields + step(1) + get_fields of its own
+    state, although every upload overlapped the previous read-back.  A step
+    queued right after a read-back does not overwrite the state being read.
+    Pageable host memory is refused."""
+    torch = pytest.importorskip("torch")
+    dt = np.float64 if precision == "fp64" else np.float32
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    bc = ("noflux", "periodic", "noflux")
+    states, want = [], []
+    for seed in (51, 52, 53):
+        pr, phi, cs, cl = wl.random_state(3, (48, 19, 70), dx=0.5, A=1.5, b=0.3, a=-0.3, seed=seed,
+                                          bc_lo=bc, bc_hi=bc)
+        states.append([torch.from_numpy(np.ascontiguousarray(x, dtype=dt)).pin_memory() for x in (phi, cs, cl)])
+        with Sim(pr, precision) as s:
+            s.set_fields(*[x.numpy() for x in states[-1]])
+            s.step(1)
+            want.append(s.get_fields())
+    outs = [[torch.empty(w[0].shape, dtype=tdt).pin_memory() for _ in range(3)] for w in want]
+    with Sim(pr, precision) as s:
+        for st, out in zip(states, outs):
+            s.set_clock(0, 0)
+            s.set_fields_step(*[x.numpy() for x in st], n=1)
+            s.get_fields_async(out_host=[o.numpy() for o in out])
+        s.sync()
+        for w, out in zip(want, outs):
+            assert all(np.array_equal(a, o.numpy()) for a, o in zip(w, out))
+        # a read-back then a step: the read-back sees the state before the step
+        dev = [torch.empty(want[2][0].shape, dtype=tdt, device="cuda") for _ in range(3)]
+        s.get_fields_async(out=dev)
+        s.step(2)
+        s.sync()
+        assert all(np.array_equal(a, d.cpu().numpy()) for a, d in zip(want[2], dev))
+        with pytest.raises(PFError, match="page-locked"):
+            s.get_fields_async(out_host=[np.empty(want[0][0].shape, dtype=dt) for _ in range(3)])
