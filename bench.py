@@ -391,6 +391,45 @@ def run_slabs(args, torch, dist, world, rank, local):
     return 0
 
 
+def run_calibrate_steady(args):
+    """Calibration of the trapping parameter A and the mobility shape b so
+    that steady pulled fronts follow the target k(V) = (k_e + V/V_D)/(1 + V/V_D),
+    V_D = 1 (the tuning of Sec. "Tailoring the partition coefficient: Selection
+    of A"): 8 fronts with V log-spaced in 0.1..0.5, 2048 cells, the steep frozen
+    gradient (0.2 per W, D_s/D_l = 0.1, k_e = 0.1) on which they reach steady
+    state within the 10^5 steps of a run, FP32 value + tangent-linear
+    derivative per iteration (pf_adjoint), Adam on (log A, log b) with A kept in
+    [0.9, 2] and b in [0.05, 1] (where the model stays finite), from A = 1.1,
+    b = 1."""
+    from paper_2303_09671_gb300 import pf
+    n, k_e = 2048, 0.1
+    vs = np.logspace(np.log10(0.1), np.log10(0.5), 8)
+    nsteps = args.steps if args.steps != 2000 else 100000
+    iters = args.calibrate if args.calibrate > 0 else 40
+    made = [wl.pulled_front_1d(N=n, dx=0.5, V=float(v), k_e=k_e, D_s=0.1, A=1.1, b=1.0, G_theta=0.2,
+                               front_cell=64) for v in vs]
+    prs = [m[0] for m in made]
+    dts = [min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / v) for pr, v in zip(prs, vs)]
+    f32 = [np.concatenate([m[i] for m in made]).astype(np.float32) for i in (1, 2, 3)]
+    kt = (k_e + vs) / (1 + vs)
+    hist = []
+    t0 = time.perf_counter()
+    theta, losses = pf.calibrate(prs[0], [n] * len(vs), vs, *f32, nsteps, kt, iters=iters, lr=0.05,
+                                 wrt=("A", "b"), dt=dts, bounds={"A": (0.9, 2.0), "b": (0.05, 1.0)},
+                                 callback=lambda it, cur, r: hist.append(r["k"].tolist()))
+    wall = time.perf_counter() - t0
+    out = {"metric": "k(V) calibration loss sum (k - k_target)^2 (8 steady pulled fronts)", "value": losses[-1],
+           "unit": "loss", "n_gpus": 1, "steps": nsteps, "higher_is_better": False, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "8 pulled fronts x 2048 cells, V log-spaced 0.1..0.5, G=0.2/W, D_s/D_l=0.1, "
+                                  "k_e=0.1, target (k_e+V)/(1+V)", "iters": iters, "lr": 0.05,
+                      "start": {"A": 1.1, "b": 1.0}, "bounds": {"A": [0.9, 2.0], "b": [0.05, 1.0]}},
+           "loss_first": losses[0], "loss_last": losses[-1], "params": theta, "wall_s": wall,
+           "V": vs.tolist(), "k_target": kt.tolist(), "k_first": hist[0], "k_last": hist[-1]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_banding(args):
     """The band-forming workload of Sec. "Oscillations and solute bands": Si-As
     pulled fronts at G = 1.4e6 K/m and D_s/D_l = 1e-3 (banding_front), pulled
@@ -718,7 +757,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="leave out the bounded kv_sweep and adjoint keys of the default line")
     ap.add_argument("--workload", default="sphere3d",
-                    choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d", "banding"])
+                    choices=["sphere3d", "kv-sweep", "adjoint", "planar1d", "perturbed2d", "banding",
+                             "calibrate-steady"])
     ap.add_argument("--mode", default="slabs", choices=["slabs", "replicas"],
                     help="N > 1: one grid cut into z-slabs with a halo exchange every step (strong "
                          "scaling), or one independent grid per rank (weak scaling)")
@@ -732,6 +772,8 @@ def main():
         return run_secondary(args)
     if args.workload == "banding":
         return run_banding(args)
+    if args.workload == "calibrate-steady":
+        return run_calibrate_steady(args)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -445,9 +445,15 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(h, e, "read-back stream");
     }
-    e = cudaEventRecord(h->rb_start, h->stream);
+    // two blocks per SM: the read-back is bound by the host link (or by DRAM for
+    // device outputs) and leaves the SMs to an upload's conversion and steps
+    int dev = 0, nsms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaEventRecord(h->rb_start, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_start, 0);
-    if (e == cudaSuccess) e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb);
+    if (e == cudaSuccess)
+        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb, 2 * nsms);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->rb);
     if (e != cudaSuccess) return cuda_fail(h, e, "read-back");
     h->rb_pending = true;

@@ -612,16 +612,17 @@ cudaError_t launch_to_state_range(const HostProblem& P, const void* phi, const v
 }
 
 cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
-                              cudaStream_t s) {
+                              cudaStream_t s, int blocks) {
     const DiagConsts C = make_diag(P, 0, 0);
     const long long n = P.cells();
+    const int nb = blocks > 0 ? blocks : diag_grid();
     if (P.precision == 1) {
-        from_state_kernel<double><<<diag_grid(), DIAG_THREADS, 0, s>>>(
+        from_state_kernel<double><<<nb, DIAG_THREADS, 0, s>>>(
             view<double>(in), n, C, (double*)phi, (double*)cs, (double*)cl);
         return cudaGetLastError();
     }
     if (in.clo == nullptr) {   // no low word of c (not a state of this library's FP32 handles)
-        from_state_kernel<float><<<diag_grid(), DIAG_THREADS, 0, s>>>(
+        from_state_kernel<float><<<nb, DIAG_THREADS, 0, s>>>(
             view<float>(in), n, C, (float*)phi, (float*)cs, (float*)cl);
         return cudaGetLastError();
     }
@@ -632,13 +633,13 @@ cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi,
     if (al(f) && al(c) && al(lo) && al(d) && al(phi) && al(cs) && al(cl)) {
         n4 = n / 4;
         if (n4 > 0)
-            from_state_f32x4_kernel<<<diag_grid(), DIAG_THREADS, 0, s>>>(
+            from_state_f32x4_kernel<<<nb, DIAG_THREADS, 0, s>>>(
                 (const float4*)f, (const float4*)c, (const float4*)lo, (const float4*)d, n4, C, (float4*)phi,
                 (float4*)cs, (float4*)cl);
     }
     const long long o = 4 * n4;
     if (o < n)
-        from_state_f32_kernel<<<diag_grid(), DIAG_THREADS, 0, s>>>(f + o, c + o, lo + o, d + o, n - o, C,
+        from_state_f32_kernel<<<nb, DIAG_THREADS, 0, s>>>(f + o, c + o, lo + o, d + o, n - o, C,
                                                                    (float*)phi + o, (float*)cs + o,
                                                                    (float*)cl + o);
     return cudaGetLastError();

@@ -96,8 +96,10 @@ struct DeviceSetup {
     cudaError_t err[MAX_DEVICES] = {};
 };
 
+// state -> (phi, c_s, c_l); blocks <= 0: the reductions' grid, else that many
+// blocks (a read-back that shares the SMs and the host link with an upload)
 cudaError_t launch_from_state(const HostProblem& P, const Fields& in, void* phi, void* cs, void* cl,
-                              cudaStream_t s);
+                              cudaStream_t s, int blocks = 0);
 
 // The checks of pf_create on a problem description (pf_api.cu): "" if valid,
 // else the reason.  stepping = false leaves out what only the time step needs
