@@ -115,16 +115,20 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // p(phi) of Eq. interpolation2 and its derivative, two lanes.  AI = false: the
 // shape parameter a is 0 and p = h (the term a (phi - 1/2) phi^2 (1-phi)^2 is
 // skipped, which leaves the result bit for bit the same)
-template <bool AI = true, typename V>
+// STD = true: the quintic h with its coefficients as literals (the same
+// operations as the general form, whose zero terms drop out exactly)
+template <bool AI = true, bool STD = false, typename V>
 __device__ __forceinline__ V vp_of(const PairConsts<V>& K, V f) {
-    const V h = vmul(vmul(f, f), vfma(f, vfma(f, vfma(f, K.h5, K.h4), K.h3), K.h2));
+    const V h = STD ? vmul(vmul(f, f), vmul(f, vfma(f, vfma(f, vlit<V>(6.0), vlit<V>(-15.0)), vlit<V>(10.0))))
+                    : vmul(vmul(f, f), vfma(f, vfma(f, vfma(f, K.h5, K.h4), K.h3), K.h2));
     if constexpr (!AI) return h;
     const V g = vmul(f, vsub(vlit<V>(1.0), f));
     return vfma(vmul(K.a_int, vsub(f, vlit<V>(0.5))), vmul(g, g), h);
 }
-template <bool AI = true, typename V>
+template <bool AI = true, bool STD = false, typename V>
 __device__ __forceinline__ V vdp_of(const PairConsts<V>& K, V f) {
-    const V dh = vmul(f, vfma(f, vfma(f, vfma(f, K.dh4, K.dh3), K.dh2), K.dh1));
+    const V dh = STD ? vmul(f, vmul(f, vfma(f, vfma(f, vlit<V>(30.0), vlit<V>(-60.0)), vlit<V>(30.0))))
+                     : vmul(f, vfma(f, vfma(f, vfma(f, K.dh4, K.dh3), K.dh2), K.dh1));
     if constexpr (!AI) return dh;
     const V g = vmul(f, vsub(vlit<V>(1.0), f));
     // d/dphi [g^2 (phi - 1/2)] = g^2 + 2 g (1 - 2 phi)(phi - 1/2) = g^2 - 4 g (phi - 1/2)^2
@@ -146,13 +150,14 @@ __device__ __forceinline__ V vdp_of(const PairConsts<V>& K, V f) {
 //   F_d = r [T_s - T_l + at],  at = (1-A) d phidot dx^2 n_phi,
 //   r = 1/(n_phi^2 + |t|^2/16 + delta^2 dx^2)
 // T2 = false: a face of a 2D grid, with one transverse direction (t2 unused)
-template <typename V, bool T2 = true, bool AI = true>
+template <typename V, bool T2 = true, bool AI = true, bool STD = false>
 __device__ __forceinline__ void face_flux(const PairConsts<V>& K, V f, V cs2, V cl2, V pds, const V n[4],
                                           const V t1[4], const V t2[4], V& Fc, V& Fd) {
     const V d2 = vsub(cs2, cl2);   // twice the face d
-    const V p = vp_of<AI>(K, f);
+    const V p = vp_of<AI, STD>(K, f);
     const V omp = vsub(vlit<V>(1.0), p);
-    const V Ms = vfma(K.Ms_c_half, cs2, K.Ms_0), Ml = vfma(K.Ml_c_half, cl2, K.Ml_0);
+    const V Ms = STD ? vmul(K.Ms_c_half, cs2) : vfma(K.Ms_c_half, cs2, K.Ms_0);
+    const V Ml = STD ? vmul(K.Ml_c_half, cl2) : vfma(K.Ml_c_half, cl2, K.Ml_0);
     const V bMl = vmul(K.b, Ml);
     const V iMbar = vrcp(vfma(bMl, p, vmul(Ms, omp)));
     const V tt = T2 ? vfma(t1[0], t1[0], vmul(t2[0], t2[0])) : vmul(t1[0], t1[0]);

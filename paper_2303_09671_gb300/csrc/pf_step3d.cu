@@ -71,7 +71,7 @@ struct PTile {
 
 __device__ __forceinline__ int slot3(int z) { return ((z % 3) + 3) % 3; }
 
-template <typename T, int TX, int TY, bool L19, bool AI>
+template <typename T, int TX, int TY, bool L19, bool AI, bool STD>
 __global__ void __launch_bounds__(TX * (TY / 2), (sizeof(T) == 4 ? 2 : 1))
 step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
               const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
@@ -210,7 +210,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V c = vpair(sR[2 * NHP + hl], sR[3 * NHP + hl]);
             const V d = vpair(sR[4 * NHP + hl], sR[5 * NHP + hl]);
             const int h = hring[j];
-            const V p = vp_of<AI>(K, f);
+            const V p = vp_of<AI, STD>(K, f);
             const V cs = vfma(vsub(vlit<V>(1.0), p), d, c);
             const V cl = vsub(c, vmul(p, d));
             const V mus = vsub(vlog(cs), K.log_ke);
@@ -262,9 +262,10 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             const V sx = vsub(bxp.a, bxm.a), sy = vpair(bc.a.y - bS.a.y, bN.a.x - bc.a.x), sz_ = vsub(bzp.a, bzm.a);
             const V lx = vsub(bxp.b, bxm.b), ly = vpair(bc.b.y - bS.b.y, bN.b.x - bc.b.x), lz = vsub(bzp.b, bzm.b);
             const V cs = cc.a, cl = cc.b, mus = bc.a, mul = bc.b;
-            const V p = vp_of<AI>(K, f), dp = vdp_of<AI>(K, f);
+            const V p = vp_of<AI, STD>(K, f), dp = vdp_of<AI, STD>(K, f);
             const V omp = vsub(vlit<V>(1.0), p);
-            const V Ms = vfma(K.Ms_c, cs, K.Ms_0), Ml = vfma(K.Ml_c, cl, K.Ml_0);
+            const V Ms = STD ? vmul(K.Ms_c, cs) : vfma(K.Ms_c, cs, K.Ms_0);
+            const V Ml = STD ? vmul(K.Ml_c, cl) : vfma(K.Ml_c, cl, K.Ml_0);
             const V bMl = vmul(K.b, Ml);
             const V Msq = vmul(Ms, omp);
             const V iMbar = vrcp(vfma(bMl, p, Msq));
@@ -328,7 +329,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         t2[1] = vsub(vadd(aPL.b, aPR.b), vadd(aML.b, aMR.b));
         t2[2] = vsub(vadd(bPL.a, bPR.a), vadd(bML.a, bMR.a));
         t2[3] = vsub(vadd(bPL.b, bPR.b), vadd(bML.b, bMR.b));
-        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b), vadd(dL, dR), n,
+        face_flux<V, true, AI, STD>(K, vmul(vlit<V>(0.5), SP[0]), vadd(cL.a, cR.a), vadd(cL.b, cR.b), vadd(dL, dR), n,
                                t1, t2, Fc, Fd);
     };
     // y faces above the two rows of the pair P (lanes: y+1/2 inside P, y+3/2
@@ -355,7 +356,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V f = vmul(vlit<V>(0.5), vpair(cP[0].x + cP[0].y, cP[0].y + cN[0].x));
         const V cs2 = vpair(cP_.a.x + cP_.a.y, cP_.a.y + cN_.a.x);
         const V cl2 = vpair(cP_.b.x + cP_.b.y, cP_.b.y + cN_.b.x);
-        face_flux<V, true, AI>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
+        face_flux<V, true, AI, STD>(K, f, cs2, cl2, vpair(dP.x + dP.y, dP.y + dN.x), n, t1, t2, Fc, Fd);
     };
     // z face between the cell 0 on plane z and the cell 1 on plane z+1: x and y
     // differences from the E/W (p/m) and N/S neighbours on both planes
@@ -375,7 +376,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const V SN[4] = {vadd(aN0.a, aN1.a), vadd(aN0.b, aN1.b), vadd(bN0.a, bN1.a), vadd(bN0.b, bN1.b)};
 #pragma unroll
         for (int k = 0; k < 4; ++k) t2[k] = vpair(SP[k].y - SS[k].y, SN[k].x - SP[k].x);
-        face_flux<V, true, AI>(K, vmul(vlit<V>(0.5), vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
+        face_flux<V, true, AI, STD>(K, vmul(vlit<V>(0.5), vadd(a0.a, a1.a)), vadd(c0.a, c1.a), vadd(c0.b, c1.b),
                                vadd(d0, d1), n, t1, t2, Fc, Fd);
     };
     // single faces (the tile's low x and low y edges, the z face below the chunk)
@@ -636,15 +637,17 @@ static cudaError_t step3d_setup(int* per_sm, int* sms) {
     if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(setup.mu);
     if (!setup.done[dev]) {
-        decltype(&step3d_kernel<T, TX, TY, true, true>) kerns[4] = {
-            step3d_kernel<T, TX, TY, false, false>, step3d_kernel<T, TX, TY, false, true>,
-            step3d_kernel<T, TX, TY, true, false>, step3d_kernel<T, TX, TY, true, true>};
-        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        decltype(&step3d_kernel<T, TX, TY, true, true, false>) kerns[8] = {
+            step3d_kernel<T, TX, TY, false, false, false>, step3d_kernel<T, TX, TY, false, true, false>,
+            step3d_kernel<T, TX, TY, true, false, false>, step3d_kernel<T, TX, TY, true, true, false>,
+            step3d_kernel<T, TX, TY, false, false, true>, step3d_kernel<T, TX, TY, false, true, true>,
+            step3d_kernel<T, TX, TY, true, false, true>, step3d_kernel<T, TX, TY, true, true, true>};
+        for (int i = 0; i < 8 && e == cudaSuccess; ++i)
             e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
         if (e != cudaSuccess) return e;
         int s = 1, p = 1;
         cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kerns[3], L::NT, L::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kerns[7], L::NT, L::BYTES);
         setup.sms[dev] = s;
         setup.per_sm[dev] = p < 1 ? 1 : p;
         setup.done[dev] = true;
@@ -672,9 +675,13 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     constexpr int TX = 32, TY = 16;
     using L = PTile<T, TX, TY>;
     // 19- or 7-point Laplacian x shape parameter a != 0 or a = 0
-    decltype(&step3d_kernel<T, TX, TY, true, true>) kerns[2][2] = {
-        {step3d_kernel<T, TX, TY, false, false>, step3d_kernel<T, TX, TY, false, true>},
-        {step3d_kernel<T, TX, TY, true, false>, step3d_kernel<T, TX, TY, true, true>}};
+    // 19- or 7-point Laplacian x shape parameter a != 0 or a = 0 x default physics
+    // (quintic h, M_i = D_i c_i: literal coefficients) or not
+    decltype(&step3d_kernel<T, TX, TY, true, true, false>) kerns[2][2][2] = {
+        {{step3d_kernel<T, TX, TY, false, false, false>, step3d_kernel<T, TX, TY, false, true, false>},
+         {step3d_kernel<T, TX, TY, true, false, false>, step3d_kernel<T, TX, TY, true, true, false>}},
+        {{step3d_kernel<T, TX, TY, false, false, true>, step3d_kernel<T, TX, TY, false, true, true>},
+         {step3d_kernel<T, TX, TY, true, false, true>, step3d_kernel<T, TX, TY, true, true, true>}}};
     const HostProblem& P = *a.prob;
     int zchunk = 0, nchunks = 0;
     cudaError_t e = step3d_chunks<T>(P, a.zchunk, &zchunk, &nchunks);
@@ -688,7 +695,8 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     const int count = a.zcount > 0 ? std::min(a.zcount, nchunks - zfirst) : nchunks;
     if (count <= 0) return cudaSuccess;
     grid.z = count;
-    auto kern = kerns[C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
+    const bool std_phys = P.interp == 0 && P.mobility == 0;
+    auto kern = kerns[std_phys ? 1 : 0][C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
