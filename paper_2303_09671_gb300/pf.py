@@ -225,12 +225,23 @@ class Sim:
         ptrs, where, _keep = self._field_ptrs(phi, cs, cl)
         _check(lib().pf_set_fields_step(self._h, *ptrs, where, int(n)), self._h)
 
+    def _device_out(self, out):
+        """Pointers of three output CUDA tensors, checked (the library cannot
+        check a raw pointer): contiguous, the grid shape, the handle's dtype."""
+        if len(out) != 3:
+            raise ValueError("three output tensors (phi, cs, cl)")
+        for a in out:
+            if (not getattr(a, "is_cuda", False) or not a.is_contiguous() or tuple(a.shape) != self.shape
+                    or a.element_size() != np.dtype(self.dtype).itemsize or not a.is_floating_point()):
+                raise ValueError("device outputs must be contiguous CUDA tensors of the grid shape and dtype")
+        return [_VP(a.data_ptr()) for a in out]
+
     def get_fields(self, out=None, out_host=None):
         """Return (phi, cs, cl) as numpy arrays, or fill the given CUDA tensors
         (out), or the given host arrays (out_host: contiguous numpy arrays of the
         grid shape and the handle's dtype, page-locked for a direct copy)."""
         if out is not None:
-            ptrs = [_VP(a.data_ptr()) for a in out]
+            ptrs = self._device_out(out)
             _check(lib().pf_get_fields(self._h, *ptrs, PF_DEVICE), self._h)
             return out
         if out_host is not None:
@@ -247,7 +258,7 @@ class Sim:
         """Queue the read-back of (phi, cs, cl) into CUDA tensors (out) or
         page-locked host arrays (out_host) without waiting; valid after sync()."""
         if out is not None:
-            ptrs, where = [_VP(a.data_ptr()) for a in out], PF_DEVICE
+            ptrs, where = self._device_out(out), PF_DEVICE
         else:
             for a in out_host:
                 if a.shape != self.shape or a.dtype != self.dtype or not a.flags.c_contiguous:

@@ -223,3 +223,34 @@ def test_halo_sides_only_on_3d_z(dim, axis, needle):
     h = ctypes.c_void_p()
     rc = pf.lib().pf_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(p), None, ctypes.byref(h))
     assert rc == pf.PF_EINVAL and needle in pf.lib().pf_last_error(None).decode()
+
+
+def test_device_outputs_are_checked_before_the_call():
+    """get_fields(out=...) and get_fields_async(out=...) hand raw pointers to
+    the library, which cannot check them: the binding refuses tensors of the
+    wrong shape, dtype or layout, or not on the GPU, before any call."""
+    s = pf.Sim.__new__(pf.Sim)
+    s.shape, s.dtype, s._h = (4, 5, 6), np.float32, None
+
+    class T:
+        def __init__(self, shape=(4, 5, 6), es=4, cuda=True, contiguous=True, fp=True):
+            self.shape, self._es, self.is_cuda, self._c, self._fp = shape, es, cuda, contiguous, fp
+
+        def is_contiguous(self):
+            return self._c
+
+        def element_size(self):
+            return self._es
+
+        def is_floating_point(self):
+            return self._fp
+
+        def data_ptr(self):
+            return 0x1000
+
+    assert len(s._device_out([T(), T(), T()])) == 3
+    for bad in (T(shape=(4, 5, 5)), T(es=8), T(cuda=False), T(contiguous=False), T(fp=False)):
+        with pytest.raises(ValueError):
+            s._device_out([T(), bad, T()])
+    with pytest.raises(ValueError):
+        s._device_out([T(), T()])
