@@ -312,10 +312,10 @@ class Sim:
         return v.value
 
     def _halo_buf(self, buf):
-        if hasattr(buf, "data_ptr"):
-            if not buf.is_cuda or not buf.is_contiguous() or buf.numel() * buf.element_size() != self.halo_bytes():
-                raise ValueError("halo buffer: a contiguous CUDA tensor of halo_bytes() bytes")
-            return _VP(buf.data_ptr()), PF_DEVICE
+        if hasattr(buf, "data_ptr"):   # a torch tensor on the GPU or on the host
+            if not buf.is_contiguous() or buf.numel() * buf.element_size() != self.halo_bytes():
+                raise ValueError("halo buffer: a contiguous tensor of halo_bytes() bytes")
+            return _VP(buf.data_ptr()), (PF_DEVICE if buf.is_cuda else PF_HOST)
         if not buf.flags.c_contiguous or buf.nbytes != self.halo_bytes():
             raise ValueError("halo buffer: a contiguous host array of halo_bytes() bytes")
         return _VP(buf.ctypes.data), PF_HOST
