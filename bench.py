@@ -72,11 +72,11 @@ FP32_LANES, MUFU_LANES = 128, 16    # per SM and clock: FP32 FMA lanes, MUFU res
 # of the kernel's device code the capture ran.  The figure is reported as null
 # as soon as those sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.333824e6 + 229.011456e6) / 256 ** 3,
+    "bytes_per_cell_update": (279.825152e6 + 228.138752e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh"),
-    "sha256": ("0ba62320a52a7cef948cada821d5df79d7c31c95ea5c48deb413111a781b42d7",
-               "ca8a8936b55cf3a8d7bbbc6ef71bd5cec65b4f4c0f6931f1105397cc5e2714b8",
+    "sha256": ("66ba95011a8c9513f334429e2c50740d63c0b223502b22a57ce76453eaac80c3",
+               "1f20de031e00e90a502b3a819635ef32b8ffbda74d768230f9bfa3e8ef2f8e27",
                "47c14bc813e01ef31966d105fe81a4bca92110885cc77bf8470a1be24dce418c"),
 }
 
@@ -210,7 +210,7 @@ def kv_brief(steps=500):
     steep-gradient pulled fronts (G = 0.2 per W, D_s/D_l = 0.1, A = b = 1, V in
     0.2..2) run to steady state by the batch's own convergence test
     (|dk/dt| < 1e-8 per unit time after 200 W of pulling), with the steady state
-    checked by mass balance: the solid 10-20 W behind the front carries c_inf."""
+    checked by mass balance: the solid 5-20 W behind the front carries c_inf."""
     import torch
     from paper_2303_09671_gb300 import pf
     lengths, vs, prs, dts, phi, cs, cl = kv_sweep_inputs()
@@ -272,12 +272,12 @@ def kv_brief(steps=500):
     for i in range(4):
         f = r["phi"][i * n:(i + 1) * n].astype(np.float64)
         j = np.where((f[:-1] >= 0.5) & (f[1:] < 0.5))[0]
-        if len(j) != 1 or j[0] < 41:
-            mb.append(None)
+        if len(j) != 1 or j[0] < 20:      # no front in the window (a fully trapping front falls back
+            mb.append(None)               # past the cold end), or too little solid behind it
             continue
         p = f ** 3 * (6 * f * f - 15 * f + 10)
         c = p * r["cs"][i * n:(i + 1) * n] + (1 - p) * r["cl"][i * n:(i + 1) * n]
-        mb.append(float(np.abs(c[j[0] - 40:j[0] - 20] - 1.0).max()))
+        mb.append(float(np.abs(c[max(0, j[0] - 40):j[0] - 10] - 1.0).max()))
     out["steady"] = {"workload": "4 pulled fronts x 2048 cells, G=0.2/W, D_s/D_l=0.1, k_e=0.1, A=b=1, FP32",
                      "V": vs4.tolist(), "converged": r["converged"].astype(int).tolist(),
                      "steps": r["steps"].tolist(), "t": r["t"].tolist(), "k_v": r["k_v"].tolist(),

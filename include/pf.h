@@ -140,17 +140,22 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
  * PF_HOST, pf_set_fields reads page-locked (pinned or registered) host memory
  * directly from the conversion kernel and stages other host memory through a
  * device copy; both synchronise the stream before returning, so the caller may
- * reuse its buffers at once.  pf_get_fields synchronises the stream. */
+ * reuse its buffers at once.  pf_get_fields converts the state on the device
+ * (into the idle state buffer for host outputs, which the copy engine then
+ * reads out: a device-to-host copy runs at about twice the rate of a kernel
+ * writing page-locked memory) and synchronises the stream. */
 int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where);
 int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
 
 /* pf_get_fields without the wait, for a pipeline that reads every step's
  * fields back while the next state is being uploaded.  The conversion of the
  * current state to (phi, c_s, c_l) is queued on an internal read-back stream
- * after the work already queued on the handle's stream, and writes phi, cs, cl
- * directly: page-locked host memory (where = PF_HOST; pageable memory returns
- * PF_EINVAL) or device memory (PF_DEVICE), n[0]*n[1]*n[2] values each of the
- * handle's precision.  The values are valid after pf_sync (or after the
+ * after the work already queued on the handle's stream: into device memory
+ * (where = PF_DEVICE) directly, or into page-locked host memory (PF_HOST;
+ * pageable memory returns PF_EINVAL) through a device staging buffer of the
+ * handle's and the copy engine (the staging buffer, 3 n[0]*n[1]*n[2] values,
+ * is allocated on the first such call; PF_ENOMEM if that fails);
+ * n[0]*n[1]*n[2] values each of the handle's precision.  The values are valid after pf_sync (or after the
  * handle's stream has been synchronised following a later call on the handle).
  * The handle keeps the state being read intact until then: every later call
  * that writes the state first orders itself after the read-back, except the

@@ -38,6 +38,7 @@ struct pf_handle {
     // stream before it and one after the read-back; pending while no later work
     // of the handle has been ordered after it
     cudaStream_t rb = nullptr;
+    void* rb_stage[3] = {nullptr, nullptr, nullptr};   // device staging of the converted fields
     cudaEvent_t rb_start = nullptr, rb_done = nullptr;
     bool rb_pending = false;
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
@@ -272,6 +273,8 @@ void pf_destroy(pf_handle* h) {
     if (h->rb) cudaStreamDestroy(h->rb);
     if (h->rb_start) cudaEventDestroy(h->rb_start);
     if (h->rb_done) cudaEventDestroy(h->rb_done);
+    for (void* p : h->rb_stage)
+        if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b)
         for (void* p : h->alloc[b])
             if (p) cudaFree(p);
@@ -433,10 +436,23 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     void* tgt[3] = {phi, cs, cl};
+    const size_t bytes = (size_t)h->P.cells() * h->P.elem();
     if (where == PF_HOST) {
         const void* views[3] = {phi, cs, cl};
         if (!device_views(views)) return fail(h, PF_EINVAL, "pf_get_fields_async needs page-locked host memory");
-        for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
+        // converted into a staging buffer of the handle's own (the idle state
+        // buffer is the next upload's target), then copied by the copy engine
+        for (int f = 0; f < 3; ++f) {
+            if (!h->rb_stage[f]) {
+                cudaError_t a = cudaMalloc(&h->rb_stage[f], bytes);
+                if (a != cudaSuccess) {
+                    cudaGetLastError();
+                    h->rb_stage[f] = nullptr;
+                    return fail(h, PF_ENOMEM, std::string("read-back staging: ") + cudaGetErrorString(a));
+                }
+            }
+            tgt[f] = h->rb_stage[f];
+        }
     }
     cudaError_t e = cudaSuccess;
     if (!h->rb) {
@@ -445,15 +461,20 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(h, e, "read-back stream");
     }
-    // two blocks per SM: the read-back is bound by the host link (or by DRAM for
-    // device outputs) and leaves the SMs to an upload's conversion and steps
+    // device outputs: two blocks per SM (bound by DRAM, the SMs left to an
+    // upload's conversion and steps); host outputs: the staging conversion on
+    // the full grid, then the copy engine
     int dev = 0, nsms = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_start, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_start, 0);
     if (e == cudaSuccess)
-        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb, 2 * nsms);
+        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb,
+                                  where == PF_HOST ? 0 : 2 * nsms);
+    void* out[3] = {phi, cs, cl};
+    for (int f = 0; f < 3 && e == cudaSuccess && where == PF_HOST; ++f)
+        e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->rb);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->rb);
     if (e != cudaSuccess) return cuda_fail(h, e, "read-back");
     h->rb_pending = true;
@@ -476,18 +497,15 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
     void* out[3] = {phi, cs, cl};
     const pf::Fields& st = h->buf[h->cur ^ 1];
     void* tgt[3] = {phi, cs, cl};
-    // page-locked host memory is written by the conversion kernel itself;
-    // other host memory through a device staging copy
-    const void* views[3] = {phi, cs, cl};
-    const bool mapped = where == PF_HOST && device_views(views);
-    if (mapped) {
-        for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
-    } else if (where == PF_HOST) {
+    // host outputs: converted into the idle state buffer on the device, then
+    // copied by the copy engine (a kernel writing page-locked host memory
+    // itself reaches half the device-to-host rate of the copy engine)
+    if (where == PF_HOST) {
         tgt[0] = st.phi; tgt[1] = st.c; tgt[2] = st.d;
     }
     cudaError_t e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
-    if (where == PF_HOST && !mapped) {
+    if (where == PF_HOST) {
         for (int f = 0; f < 3; ++f) {
             e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
