@@ -39,6 +39,7 @@ struct pf_handle {
     // of the handle has been ordered after it
     cudaStream_t rb = nullptr;
     void* rb_stage[3] = {nullptr, nullptr, nullptr};   // device staging of the converted fields
+    bool rb_copy = false;        // read-backs to host: staged + copy engine (true) or kernel-written
     cudaEvent_t rb_start = nullptr, rb_done = nullptr;
     bool rb_pending = false;
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
@@ -228,6 +229,7 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
     if (const char* oc = std::getenv("PF_OVCHUNK")) h->ovchunk = std::atoi(oc);
     if (const char* g = std::getenv("PF_GENERIC")) h->generic = std::atoi(g) != 0;   // cross-check kernel
+    if (const char* r = std::getenv("PF_READBACK")) h->rb_copy = std::strcmp(r, "copy") == 0;
 
     h->halo[0] = P.bc_lo[2] == PF_BC_HALO;
     h->halo[1] = P.bc_hi[2] == PF_BC_HALO;
@@ -440,8 +442,13 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
     if (where == PF_HOST) {
         const void* views[3] = {phi, cs, cl};
         if (!device_views(views)) return fail(h, PF_EINVAL, "pf_get_fields_async needs page-locked host memory");
-        // converted into a staging buffer of the handle's own (the idle state
-        // buffer is the next upload's target), then copied by the copy engine
+        for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
+    }
+    // PF_READBACK=copy: host outputs converted into a staging buffer of the
+    // handle's own (the idle state buffer is the next upload's target), then
+    // copied by the copy engine; else written by the conversion kernel
+    const bool staged = where == PF_HOST && h->rb_copy;
+    if (staged) {
         for (int f = 0; f < 3; ++f) {
             if (!h->rb_stage[f]) {
                 cudaError_t a = cudaMalloc(&h->rb_stage[f], bytes);
@@ -461,19 +468,18 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(h, e, "read-back stream");
     }
-    // device outputs: two blocks per SM (bound by DRAM, the SMs left to an
-    // upload's conversion and steps); host outputs: the staging conversion on
-    // the full grid, then the copy engine
+    // written by the kernel: two blocks per SM (bound by the link or DRAM, the
+    // SMs left to an upload's conversion and steps); staged: the conversion
+    // on the full grid, then the copy engine
     int dev = 0, nsms = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_start, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_start, 0);
     if (e == cudaSuccess)
-        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb,
-                                  where == PF_HOST ? 0 : 2 * nsms);
+        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb, staged ? 0 : 2 * nsms);
     void* out[3] = {phi, cs, cl};
-    for (int f = 0; f < 3 && e == cudaSuccess && where == PF_HOST; ++f)
+    for (int f = 0; f < 3 && e == cudaSuccess && staged; ++f)
         e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->rb);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->rb);
     if (e != cudaSuccess) return cuda_fail(h, e, "read-back");
@@ -497,15 +503,19 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
     void* out[3] = {phi, cs, cl};
     const pf::Fields& st = h->buf[h->cur ^ 1];
     void* tgt[3] = {phi, cs, cl};
-    // host outputs: converted into the idle state buffer on the device, then
-    // copied by the copy engine (a kernel writing page-locked host memory
-    // itself reaches half the device-to-host rate of the copy engine)
-    if (where == PF_HOST) {
+    // page-locked host memory is written by the conversion kernel itself
+    // (unless PF_READBACK=copy); other host memory through a device staging
+    // copy (the idle state buffer) and the copy engine
+    const void* views[3] = {phi, cs, cl};
+    const bool mapped = where == PF_HOST && !h->rb_copy && device_views(views);
+    if (mapped) {
+        for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
+    } else if (where == PF_HOST) {
         tgt[0] = st.phi; tgt[1] = st.c; tgt[2] = st.d;
     }
     cudaError_t e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "state conversion");
-    if (where == PF_HOST) {
+    if (where == PF_HOST && !mapped) {
         for (int f = 0; f < 3; ++f) {
             e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
