@@ -155,12 +155,12 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
  * pageable memory returns PF_EINVAL) through a device staging buffer of the
  * handle's and the copy engine (the staging buffer, 3 n[0]*n[1]*n[2] values,
  * is allocated on the first such call; PF_ENOMEM if that fails);
- * n[0]*n[1]*n[2] values each of the handle's precision.  The values are valid after pf_sync (or after the
- * handle's stream has been synchronised following a later call on the handle).
- * The handle keeps the state being read intact until then: every later call
- * that writes the state first orders itself after the read-back, except the
- * upload of pf_set_fields_step, which converts into the other state buffer and
- * so overlaps the read-back (only its step waits).  The handle creates the
+ * n[0]*n[1]*n[2] values each of the handle's precision.  The values are valid after pf_sync.
+ * The handle keeps the state being read intact until the read-back has read
+ * it: every later call that writes the state first orders itself after that
+ * read (not after the copies to the host), except the upload of
+ * pf_set_fields_step, which converts into the other state buffer and so
+ * overlaps the read-back (only its step waits for the read).  The handle creates the
  * stream and its events on first use and frees them in pf_destroy. */
 int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where);
 

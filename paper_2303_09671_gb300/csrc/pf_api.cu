@@ -39,7 +39,7 @@ struct pf_handle {
     // of the handle has been ordered after it
     cudaStream_t rb = nullptr;
     void* rb_stage[3] = {nullptr, nullptr, nullptr};   // device staging of the converted fields
-    bool rb_copy = false;        // read-backs to host: staged + copy engine (true) or kernel-written
+    bool rb_copy = true;         // read-backs to host: staged + copy engine (true) or kernel-written
     // pf_set_fields_step from page-locked host memory: slabs copied by the copy
     // engine into a device staging buffer (on their own stream, one event per
     // slab) and converted from there; up_kernel = the conversion reads the host
@@ -49,6 +49,7 @@ struct pf_handle {
     std::vector<cudaEvent_t> cp_ev;
     bool up_kernel = false;
     cudaEvent_t rb_start = nullptr, rb_done = nullptr;
+    cudaEvent_t rb_read = nullptr;   // the read-back has read the state (before its host copies)
     bool rb_pending = false;
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
     int ovchunk = 16;            // z planes per slab and CTA in pf_set_fields_step
@@ -90,11 +91,12 @@ int cuda_fail(pf_handle* h, cudaError_t e, const char* what) {
     return fail(h, PF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// order the handle's stream after a pending pf_get_fields_async (before any
-// work that may overwrite the state it reads)
+// order the handle's stream after the state read of a pending
+// pf_get_fields_async (before any work that may overwrite that state; its
+// copies to the host may still run)
 int join_readback(pf_handle* h) {
     if (!h->rb_pending) return PF_OK;
-    cudaError_t e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);
+    cudaError_t e = cudaStreamWaitEvent(h->stream, h->rb_read, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "read-back join");
     h->rb_pending = false;
     return PF_OK;
@@ -237,7 +239,7 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
     if (const char* oc = std::getenv("PF_OVCHUNK")) h->ovchunk = std::atoi(oc);
     if (const char* g = std::getenv("PF_GENERIC")) h->generic = std::atoi(g) != 0;   // cross-check kernel
-    if (const char* r = std::getenv("PF_READBACK")) h->rb_copy = std::strcmp(r, "copy") == 0;
+    if (const char* r = std::getenv("PF_READBACK")) h->rb_copy = std::strcmp(r, "direct") != 0;
     if (const char* u = std::getenv("PF_UPLOAD")) h->up_kernel = std::strcmp(u, "kernel") == 0;
 
     h->halo[0] = P.bc_lo[2] == PF_BC_HALO;
@@ -284,6 +286,7 @@ void pf_destroy(pf_handle* h) {
     if (h->rb) cudaStreamDestroy(h->rb);
     if (h->rb_start) cudaEventDestroy(h->rb_start);
     if (h->rb_done) cudaEventDestroy(h->rb_done);
+    if (h->rb_read) cudaEventDestroy(h->rb_read);
     for (void* p : h->rb_stage)
         if (p) cudaFree(p);
     for (void* p : h->up_stage)
@@ -445,7 +448,7 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
     const pf::Fields& out = h->buf[dst_buf];
     const bool zper = P.bc_lo[2] == PF_BC_PERIODIC;
     for (int i = 1; i < pf_handle::OV_STREAMS && e == cudaSuccess && h->rb_pending; ++i)
-        e = cudaStreamWaitEvent(h->ov[i], h->rb_done, 0);
+        e = cudaStreamWaitEvent(h->ov[i], h->rb_read, 0);
     for (int j = 0; j < nch && e == cudaSuccess; ++j) {
         const int z0 = j * zchunk, z1 = std::min(nz, z0 + zchunk);
         int need = std::min(nch - 1, std::min(nz - 1, z1 + 1) / zchunk);
@@ -496,9 +499,9 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
         if (!device_views(views)) return fail(h, PF_EINVAL, "pf_get_fields_async needs page-locked host memory");
         for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
     }
-    // PF_READBACK=copy: host outputs converted into a staging buffer of the
-    // handle's own (the idle state buffer is the next upload's target), then
-    // copied by the copy engine; else written by the conversion kernel
+    // host outputs converted into a staging buffer of the handle's own (the
+    // idle state buffer is the next upload's target), then copied by the copy
+    // engine (PF_READBACK=direct: written by the conversion kernel itself)
     const bool staged = where == PF_HOST && h->rb_copy;
     if (staged) {
         for (int f = 0; f < 3; ++f) {
@@ -518,6 +521,7 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
         e = cudaStreamCreateWithFlags(&h->rb, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_start, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_read, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(h, e, "read-back stream");
     }
     // written by the kernel: two blocks per SM (bound by the link or DRAM, the
@@ -530,6 +534,7 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_start, 0);
     if (e == cudaSuccess)
         e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb, staged ? 0 : 2 * nsms);
+    if (e == cudaSuccess) e = cudaEventRecord(h->rb_read, h->rb);
     void* out[3] = {phi, cs, cl};
     for (int f = 0; f < 3 && e == cudaSuccess && staged; ++f)
         e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->rb);
@@ -542,7 +547,9 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
 int pf_sync(pf_handle* h) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (int rc = join_readback(h)) return rc;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = cudaSuccess;
+    if (h->rb) e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);   // the copies to the host too
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     return PF_OK;
 }
@@ -555,9 +562,9 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
     void* out[3] = {phi, cs, cl};
     const pf::Fields& st = h->buf[h->cur ^ 1];
     void* tgt[3] = {phi, cs, cl};
-    // page-locked host memory is written by the conversion kernel itself
-    // (unless PF_READBACK=copy); other host memory through a device staging
-    // copy (the idle state buffer) and the copy engine
+    // host memory through a device staging copy (the idle state buffer) and the
+    // copy engine (PF_READBACK=direct: page-locked memory written by the
+    // conversion kernel itself, at about half the device-to-host rate)
     const void* views[3] = {phi, cs, cl};
     const bool mapped = where == PF_HOST && !h->rb_copy && device_views(views);
     if (mapped) {
