@@ -900,8 +900,8 @@ def main():
                              "bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * cells,
                     "d2h_bytes_per_step": 3 * 4 * cells, "steps": ke,
-                    "path": "pf_set_fields_step (upload overlapped with the step) + pf_get_fields_async to pinned "
-                            "host memory (each read-back overlapped with the next upload)"},
+                    "path": "pf_set_fields_step (copy-engine upload overlapped with the step) + pf_get_fields_async "
+                            "to pinned host memory (copy-engine read-back overlapped with the next upload)"},
             "e2e_solute_only": {"value": e2e_sol_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * cells,
                                 "d2h_bytes_per_step": 8, "steps": ke,
                                 "path": "pf_set_fields_step + pf_solute_total_async (8-byte result per step)"},
