@@ -121,3 +121,44 @@ def test_sphere_256_cubed_energy_and_solute_over_300_steps():
     assert np.all(dF <= 1e-12 * abs(F[0])), dF.max()
     assert F[-1] < F[0]
     assert abs(S1 - S0) <= 1e-7 * abs(S0)
+
+
+def test_planar_1d_fp64_full_configuration():
+    """The 1D planar front exactly as configured (N = 1024, dx = W/4, FP64,
+    front at cell 256, k_e = 0.1, undercooling 0.3, D_s/D_l = 1e-4, no-flux,
+    0.9 of the stable dt, 2x10^4 steps) against the oracle: every field at the
+    FP64 bar, F_h recorded after every step on the device never increasing and
+    equal to the oracle's at the last step, the front position equal."""
+    pr, phi, cs, cl = wl.planar_1d(A=2.0, b=1.0)
+    assert pr["n"] == (1024,) and pr["dx"] == 0.25
+    st = oracle.State(pr, phi, cs, cl)
+    st.step(20000)
+    with Sim(pr, "fp64") as s:
+        s.set_fields(phi, cs, cl)
+        F = s.step_energies(20000)
+        g = s.get_fields()
+        xf, _, cm = s.front()
+    st.inputs = (phi, cs, cl, 20000)
+    assert_fields(st, g, TOL64, pr, reps=1)
+    assert np.all(np.diff(F) <= 1e-12 * abs(F[0]))
+    assert abs(F[-1] - st.energy()) <= 1e-12 * abs(F[-1])
+    oxf, ocm = st.front()
+    assert abs(xf - oxf) <= 1e-12 * abs(oxf) and abs(cm - ocm) <= 1e-12 * abs(ocm)
+
+
+def test_perturbed_2d_1024_fp32_energy_and_solute_over_1e4_steps():
+    """The 2D perturbed front at its full size (1024^2 FP32, 9-point
+    Laplacian, periodic along the front, 10^4 steps) through properties that
+    hold at any size: F_h never increases from one step to the next (check
+    (a)) and the solute drifts by at most 1e-7 relative (check (b))."""
+    pr, phi, cs, cl = wl.perturbed_front_2d(A=1.0, b=1.0)
+    assert tuple(pr["n"]) == (1024, 1024) and pr["G_theta"] == 0.0
+    with Sim(pr, "fp32") as s:
+        s.set_fields(*(np.asarray(a, np.float32) for a in (phi, cs, cl)))
+        S0 = s.solute_total()
+        F = s.step_energies(10000)
+        S1 = s.solute_total()
+    dF = np.diff(F)
+    print(f"F_h {F[0]:.9e} -> {F[-1]:.9e}, largest increase {dF.max():.2e}, solute drift {abs(S1 - S0) / S0:.2e}")
+    assert np.all(dF <= 1e-12 * abs(F[0])), dF.max()
+    assert abs(S1 - S0) <= 1e-7 * abs(S0)
