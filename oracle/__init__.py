@@ -121,6 +121,7 @@ def lib():
             L.orc_solute.argtypes = [P, dp, dp, dp]
             L.orc_solute.restype = ctypes.c_double
             L.orc_front.argtypes = [P, C, dp, dp, dp, dp, dp]
+            L.orc_mixture.argtypes = [P, dp, dp, dp, ctypes.c_int64, dp, dp]
             L.orc_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -178,6 +179,18 @@ def point(p: dict, phi: float, cs: float, cl: float, theta: float) -> dict:
     out = (ctypes.c_double * len(POINT_NAMES))()
     lib().orc_point(ctypes.byref(_params(p)), phi, cs, cl, theta, out)
     return dict(zip(POINT_NAMES, list(out)))
+
+
+def mixture(p: dict, phi, cs, cl):
+    """(p(phi), c = p c_s + (1 - p) c_l) per cell, for arrays of one shape."""
+    phi, cs, cl = (np.ascontiguousarray(a, dtype=np.float64) for a in (phi, cs, cl))
+    if not (phi.shape == cs.shape == cl.shape):
+        raise ValueError("phi, c_s, c_l must have one shape")
+    pv, cv = np.empty_like(phi), np.empty_like(phi)
+    if lib().orc_mixture(ctypes.byref(_params(p)), _dptr(phi), _dptr(cs), _dptr(cl), phi.size,
+                         _dptr(pv), _dptr(cv)) != 0:
+        raise ValueError("oracle: invalid parameters")
+    return pv, cv
 
 
 class State:

@@ -555,6 +555,20 @@ double orc_solute(const orc_params* P, const double* phi, const double* cs,
     return tot * pow(P->dx, P->dim);
 }
 
+/* Per cell: p(phi) and the mixture c = p c_s + (1 - p) c_l (Eq. model1 with
+ * g = p), the terms that orc_solute sums. */
+int orc_mixture(const orc_params* P, const double* phi, const double* cs,
+                const double* cl, int64_t n, double* p_out, double* c_out) {
+    if (!valid_params(P) || n < 0) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t u = 0; u < n; ++u) {
+        double p = p_of(P, phi[u]);
+        if (p_out) p_out[u] = p;
+        if (c_out) c_out[u] = p * cs[u] + (1.0 - p) * cl[u];
+    }
+    return 0;
+}
+
 int orc_front(const orc_params* P, const orc_clock* clk, const double* phi,
               const double* cs, const double* cl, double* x_front, double* c_max) {
     if (!valid_params(P)) return -1;

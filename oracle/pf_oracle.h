@@ -83,6 +83,10 @@ double orc_energy(const orc_params* P, const orc_clock* clk, const double* phi,
                   const double* cs, const double* cl);
 double orc_solute(const orc_params* P, const double* phi, const double* cs,
                   const double* cl);
+/* p(phi) and the mixture c = p c_s + (1 - p) c_l of each of n cells (either
+ * output may be NULL).  Returns 0, or -1 on invalid arguments. */
+int orc_mixture(const orc_params* P, const double* phi, const double* cs,
+                const double* cl, int64_t n, double* p_out, double* c_out);
 /* front position (lab frame, largest phi=0.5 crossing along x over all rows)
  * and c_max.  x_front = NaN when no row has a crossing. */
 int orc_front(const orc_params* P, const orc_clock* clk, const double* phi,

@@ -74,11 +74,8 @@ def assert_fields(st, g, tol, pr=None, reps=2):
         assert 8.0 * spread[i] <= SPREAD_CAP, f"{name}: oracle spread {spread[i]:.1e} above the cap"
         assert e <= lim, f"{name}: relative error {e:.3e} > {lim:.1e} (oracle spread {spread[i]:.1e})"
     if pr is not None:
-        P = oracle.point
-        pg = np.vectorize(lambda f: P(pr, f, 1.0, 1.0, 0.0)["p"])(g[0])
-        po = np.vectorize(lambda f: P(pr, f, 1.0, 1.0, 0.0)["p"])(st.phi)
-        cg = pg * g[1] + (1 - pg) * g[2]
-        co = po * st.cs + (1 - po) * st.cl
+        _, cg = oracle.mixture(pr, *g)
+        _, co = oracle.mixture(pr, st.phi, st.cs, st.cl)
         lim_c = max(tol, 8.0 * spread[0])
         e = rel_err(cg, co)
         print(f"parity c: error {e:.2e}, bar {lim_c:.1e}")
@@ -226,8 +223,7 @@ def test_fp64_diagnostics():
 # gradients of phi ~ 1 tails at all.
 
 def total_c(pr, phi, cs, cl):
-    p = np.vectorize(lambda f: oracle.point(pr, f, 1.0, 1.0, 0.0)["p"])(phi)
-    return p, p * cs + (1 - p) * cl
+    return oracle.mixture(pr, phi, cs, cl)
 
 
 def check_fp32(pr, st, g, S0g, S1g, tol_c=1e-5, tol_phi=1e-4, tol_phase=1e-4):

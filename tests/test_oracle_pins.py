@@ -216,6 +216,24 @@ def test_total_solute_conserved(maker, nsteps):
     assert abs(st.solute() - S0) <= 2e-13 * abs(S0)
 
 
+def test_mixture_is_the_pointwise_p_and_the_solute_density():
+    """oracle.mixture (the per-cell helper the full-size GPU tests use) gives
+    the p(phi) of the pointwise evaluator at every cell, including the pure
+    phases (p(0) = 0, p(1) = 1), and c = p c_s + (1 - p) c_l summed times
+    dx^dim is the oracle's S_h."""
+    for interp in ("quintic", "cubic"):
+        pr, phi, cs, cl = wl.random_state(2, (30, 11), A=1.5, b=0.3, a=-0.3, seed=3, interp=interp)
+        phi = phi.copy()
+        phi[0, 0], phi[0, 1] = 0.0, 1.0
+        p, c = oracle.mixture(pr, phi, cs, cl)
+        ref = np.array([oracle.point(pr, f, 1.0, 1.0, 0.0)["p"] for f in phi.ravel()]).reshape(phi.shape)
+        assert np.array_equal(p, ref)
+        assert p[0, 0] == 0.0 and p[0, 1] == 1.0
+        assert np.allclose(c, ref * cs + (1 - ref) * cl, rtol=1e-15, atol=0)
+        S = oracle.State(pr, phi, cs, cl).solute()
+        assert abs(c.sum() * pr["dx"] ** 2 - S) <= 1e-13 * abs(S)
+
+
 @pytest.mark.parametrize("maker,nsteps", [
     (lambda: wl.planar_1d(N=512, A=2.0, b=1.0), 4000),
     (lambda: wl.perturbed_front_2d(nx=128, ny=128, front=40, seed=20, A=1.5, b=0.3), 1500),
