@@ -130,7 +130,12 @@ typedef struct pf_handle pf_handle;
  * of the paired two-lane kernels (a cross-check; same results to rounding),
  * PF_ZCHUNK=<planes> fixes the z-chunk of the 3D kernel,
  * PF_OVCHUNK=<planes> the slab length of pf_set_fields_step (default 16, at most
- * the z-chunk when that is fixed). */
+ * the z-chunk when that is fixed), PF_TMA=0 stages every plane of the 3D FP32
+ * step with per-cell copies instead of tensor-memory-accelerator boxes (a
+ * cross-check; identical results bit for bit; the boxes are used where n[0]
+ * is a multiple of 4 and no x or y side is periodic), and
+ * PF_TEST_DROP_COPIES=1 leaves the box copies out, so that the step's
+ * bounded wait runs out (tests of PF_ETIMEOUT only). */
 int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params,
               void* stream, pf_handle** out);
 
@@ -164,7 +169,15 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
  * stream and its events on first use and frees them in pf_destroy. */
 int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where);
 
-/* Wait for every piece of work of the handle, read-backs included. */
+/* Wait for every piece of work of the handle, read-backs included.
+ *
+ * The 3D FP32 step waits on an mbarrier for the boxes of each plane, with a
+ * time limit of half a second per wait.  A wait that runs out sets a device
+ * flag of the handle, and the kernel finishes without waiting again (its
+ * output state is then not valid).  pf_sync, pf_get_fields, pf_energy,
+ * pf_solute_total, pf_front and pf_step_energies read the flag with the
+ * synchronisation they already do: PF_ETIMEOUT once, after which the flag is
+ * cleared. */
 int pf_sync(pf_handle* h);
 
 /* Advance n >= 0 forward-Euler steps (stream-ordered, no host sync). */

@@ -19,8 +19,9 @@ struct pf_handle {
     int cur = 0;
     int64_t step = 0, shifts = 0;
     double* scratch = nullptr;   // diagnostics partials
-    double* dres = nullptr;      // device results (4 doubles)
-    double* hres = nullptr;      // pinned host results (4 doubles)
+    double* dres = nullptr;      // device results (4 doubles), then the step kernels' error flag
+    double* hres = nullptr;      // pinned host results (4 doubles), then the flag's copy
+    int* derr = nullptr;         // the flag: a bounded wait in a step kernel ran out
     double* drec = nullptr;      // per-step (F_h, S_h) records of pf_step_energies
     int64_t rec_cap = 0;
     // pf_set_fields_step: a conversion stream, chunk streams, one event per slab
@@ -54,6 +55,8 @@ struct pf_handle {
     int zchunk = 0;              // z planes per CTA (3D); 0 = automatic
     int ovchunk = 16;            // z planes per slab and CTA in pf_set_fields_step
     bool generic = false;        // run 2D / 3D through the generic kernel (cross-check)
+    bool no_tma = false;         // 3D: per-cell plane copies instead of TMA boxes (cross-check)
+    bool drop_copies = false;    // 3D TMA: copies left out, to test the bounded wait
     bool have_front = false;
     double last_xf = 0.0, last_t = 0.0;
     std::string err;
@@ -122,6 +125,17 @@ double stable_dt(const pf_grid* g, const pf_params* p) {
     const double dt_phi = 2.0 / (p->M_phi * (lam * p->sigma + 2.0 * p->H));
     const double dt_c = 2.0 / (lam * effective_dmax(p));
     return std::fmin(dt_phi, dt_c);
+}
+
+// the step kernels' error flag, copied to hres[4] on the handle's stream by
+// the caller's copy: PF_ETIMEOUT (and the flag cleared) if it was set
+int step_error(pf_handle* h) {
+    if (*reinterpret_cast<const int*>(h->hres + 4) == 0) return PF_OK;
+    *reinterpret_cast<int*>(h->hres + 4) = 0;
+    cudaError_t e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error flag reset");
+    return fail(h, PF_ETIMEOUT, "a step kernel's bounded wait for its plane copies ran out; the state is not valid");
 }
 
 }  // namespace
@@ -239,6 +253,8 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
     if (const char* zc = std::getenv("PF_ZCHUNK")) h->zchunk = std::atoi(zc);   // tuning override
     if (const char* oc = std::getenv("PF_OVCHUNK")) h->ovchunk = std::atoi(oc);
     if (const char* g = std::getenv("PF_GENERIC")) h->generic = std::atoi(g) != 0;   // cross-check kernel
+    if (const char* t = std::getenv("PF_TMA")) h->no_tma = std::atoi(t) == 0;           // cross-check staging
+    if (const char* t = std::getenv("PF_TEST_DROP_COPIES")) h->drop_copies = std::atoi(t) != 0;
     if (const char* r = std::getenv("PF_READBACK")) h->rb_copy = std::strcmp(r, "direct") != 0;
     if (const char* u = std::getenv("PF_UPLOAD")) h->up_kernel = std::strcmp(u, "kernel") == 0;
 
@@ -267,8 +283,12 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
         }
     }
     cudaError_t e = cudaMalloc(&h->scratch, pf::diag_scratch_doubles(P) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dres, 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->hres, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dres, 5 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->hres, 5 * sizeof(double));
+    if (e == cudaSuccess) {
+        h->derr = reinterpret_cast<int*>(h->dres + 4);
+        e = cudaMemset(h->derr, 0, sizeof(int));
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         pf_destroy(h);
@@ -469,6 +489,9 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
         a.zcount = 1;
         a.use_generic = false;
         a.stream = ks;
+        a.err = h->derr;
+        a.no_tma = h->no_tma;
+        a.drop_copies = h->drop_copies;
         e = pf::launch_step(a);
     }
     // the handle's stream continues after every chunk
@@ -549,9 +572,10 @@ int pf_sync(pf_handle* h) {
     if (int rc = join_readback(h)) return rc;
     cudaError_t e = cudaSuccess;
     if (h->rb) e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);   // the copies to the host too
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hres + 4, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
-    return PF_OK;
+    return step_error(h);
 }
 
 int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
@@ -580,9 +604,10 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
         }
     }
-    e = cudaStreamSynchronize(h->stream);
+    e = cudaMemcpyAsync(h->hres + 4, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
-    return PF_OK;
+    return step_error(h);
 }
 
 int pf_step(pf_handle* h, int64_t n) {
@@ -609,6 +634,9 @@ int pf_step(pf_handle* h, int64_t n) {
         a.zchunk = h->zchunk;
         a.use_generic = h->generic;
         a.stream = h->stream;
+        a.err = h->derr;
+        a.no_tma = h->no_tma;
+        a.drop_copies = h->drop_copies;
         cudaError_t e = pf::launch_step(a);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
         h->cur ^= 1;
@@ -627,11 +655,11 @@ int pf_step(pf_handle* h, int64_t n) {
 }
 
 static int fetch_results(pf_handle* h, int count) {
-    cudaError_t e = cudaMemcpyAsync(h->hres, h->dres, count * sizeof(double), cudaMemcpyDeviceToHost,
-                                    h->stream);
+    (void)count;   // the results and the error flag, in one copy
+    cudaError_t e = cudaMemcpyAsync(h->hres, h->dres, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "result copy");
-    return PF_OK;
+    return step_error(h);
 }
 
 static int energy_solute(pf_handle* h, bool with_energy) {
@@ -740,8 +768,10 @@ int pf_step_energies(pf_handle* h, int64_t n, double* F) {
         if (int rc = one()) return rc;
     std::vector<double> rec(2 * (size_t)n);
     e = cudaMemcpyAsync(rec.data(), h->drec, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hres + 4, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "record copy");
+    if (int rc = step_error(h)) return rc;
     bool finite = true;
     for (int64_t s = 0; s < n; ++s) {
         F[s] = rec[2 * s];

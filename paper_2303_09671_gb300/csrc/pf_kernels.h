@@ -44,6 +44,9 @@ struct StepLaunch {
     int zfirst = 0, zcount = 0;   // 3D: run z-chunks [zfirst, zfirst + zcount) only; zcount <= 0: all
     bool use_generic;       // 2D / 3D: the generic (1D/2D/3D) kernel instead of the paired one
     cudaStream_t stream;
+    int* err = nullptr;     // device flag a step kernel sets when a bounded wait runs out (or NULL)
+    bool no_tma = false;    // 3D: per-cell cp.async plane loads even where TMA boxes apply
+    bool drop_copies = false;   // 3D TMA: arrive without issuing the copies (tests the bounded wait)
 };
 
 cudaError_t launch_step(const StepLaunch& a);

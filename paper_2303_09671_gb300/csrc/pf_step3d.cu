@@ -30,9 +30,11 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include "pf_internal.cuh"
 #include "pf_kernels.h"
 #include "pf_lanes.cuh"
+#include "pf_tma.cuh"
 
 namespace pf {
 
@@ -53,7 +55,6 @@ struct PTile {
     static constexpr int OQ = 0, OV = 0, OD = 0, OF = 0;    // base shifts (elements)
     static constexpr int HP = HX * HYP, RP = HP;            // plane stride
     static constexpr int FXP = TX + 1;                      // x-face row pitch
-    static constexpr int NHP = (NH + 15) / 16 * 16;         // staging lane-plane stride
     static constexpr int JH = (NH + NT - 1) / NT;
     static constexpr size_t OFF_A = 0;                                   // {phi, Y}, 4 planes
     static constexpr size_t OFF_B = OFF_A + sizeof(Q) * 4 * HP;          // {mu_s, mu_l}, 4 planes
@@ -62,29 +63,44 @@ struct PTile {
     static constexpr size_t OFF_D = OFF_P + sizeof(V) * 3 * HP;          // dx^2 phidot, 2 planes
     static constexpr size_t OFF_FX = OFF_D + sizeof(V) * 2 * RP;         // x faces {F_c, F_d}
     static constexpr size_t OFF_FY = OFF_FX + sizeof(Q) * (TYP * FXP);       // upper y face {F_c, F_d}
-    static constexpr size_t OFF_R = OFF_FY + sizeof(V) * (TYP + 1) * TX;     // next plane: phi, c, d per lane
-    static constexpr size_t OFF_O = OFF_R + sizeof(V) * 3 * NHP;             // own c, d, c_lo per lane
-    static constexpr size_t BYTES = OFF_O + sizeof(V) * 3 * NT;
+    // Staging of one plane.  TMA: the box of cells x0-4 .. x0+TX+3, y0-2 ..
+    // y0+TY+1 per field, as the tensor-memory accelerator writes it (rows of
+    // BXW elements; x starts 4 cells left of the tile so that the box's first
+    // element is 16-byte aligned), each field's box followed by a slot for the
+    // Dirichlet state (field stride RS, 128-byte aligned); the own state of the
+    // plane being updated in boxes of the same shape.  cp.async: the pair
+    // cells lane-planar, [field][lane][NHP], and the own state [field][lane][NT].
+    static constexpr int BXW = TX + 8, BH = TY + 4, BOX = BXW * BH;
+    static constexpr int RS = BOX + 128 / (int)sizeof(T);
+    static constexpr int NHP = (NH + 15) / 16 * 16;
+    static constexpr size_t OFF_R = (OFF_FY + sizeof(V) * (TYP + 1) * TX + 127) / 128 * 128;   // phi, c, d
+    static constexpr size_t OFF_O = OFF_R + sizeof(T) * (3 * RS > 6 * NHP ? 3 * RS : 6 * NHP);   // c, d, c_lo
+    static constexpr size_t OFF_BAR = OFF_O + sizeof(T) * (3 * RS > 6 * NT ? 3 * RS : 6 * NT);   // mbarrier
+    static constexpr size_t BYTES = OFF_BAR + 16;
+    static_assert((sizeof(T) * RS) % 128 == 0 && OFF_BAR % 8 == 0, "staging boxes 128-byte aligned");
     static constexpr int NB = NR - NT;   // ring cells besides the threads' own pairs
     static_assert(NB == 2 * RW + 2 * TYP && NB <= NT, "ring = own pairs + border");
 };
 
 __device__ __forceinline__ int slot3(int z) { return ((z % 3) + 3) % 3; }
 
-template <typename T, int TX, int TY, bool L19, bool AI, bool STD>
+template <typename T, int TX, int TY, bool L19, bool AI, bool STD, bool TMA>
 __global__ void __launch_bounds__(TX * (TY / 2), (sizeof(T) == 4 ? 2 : 1))
 step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T* __restrict__ d_in,
               const T* __restrict__ clo_in, T* __restrict__ phi_out, T* __restrict__ c_out,
               T* __restrict__ d_out, T* __restrict__ clo_out, const PairConsts<typename Lanes<T>::V> K,
-              const GridConsts<T> G, int zchunk, int zbase) {
+              const GridConsts<T> G, int zchunk, int zbase, const __grid_constant__ CUtensorMap tm_phi,
+              const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_d,
+              const __grid_constant__ CUtensorMap tm_clo, int flags, int zpad, int* __restrict__ err) {
     using L = PTile<T, TX, TY>;
     using V = typename L::V;
     using Q = typename L::Q;
     constexpr int HX = L::HX, HP = L::HP, RX = L::RX, RP = L::RP, NT = L::NT, TYP = L::TYP;
     constexpr int HW = L::HW, NH = L::NH, NHP = L::NHP, RW = L::RW, FXP = L::FXP;
+    constexpr int BXW = L::BXW, BH = L::BH, BOX = L::BOX, RS = L::RS;
     static_assert(HP < 4096, "tile too large for the packed ring descriptors");
     static_assert(NT >= 32 + TX && TYP <= 32, "edge faces need warps 0 and 1");
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     Q* sA = reinterpret_cast<Q*>(smem + L::OFF_A) + L::OQ;
     Q* sB = reinterpret_cast<Q*>(smem + L::OFF_B) + L::OQ;
     Q* sC = reinterpret_cast<Q*>(smem + L::OFF_C) + L::OQ;
@@ -100,21 +116,36 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     const long long sz = (long long)nx * ny;
 
     // ---- work lists, fixed for the whole z-march
-    // halo pair cells this thread loads (staging index tid + j NT) and converts
-    // (ring index hring[j] in the pitched plane arrays)
-    int hoff[L::JH][2];   // in-plane offsets of the two rows of each loaded pair cell, -1: ghost
+    // halo pair cells this thread converts (pair index tid + j NT, ring index
+    // hring[j] in the pitched plane arrays).  TMA: the plane arrives as a box
+    // per field (one thread issues it) and loc[j][l] is the box index of the
+    // source of row l of each pair cell (a mirror ghost's image lies inside the
+    // box; cells further than the ghost width from the domain, present in
+    // partial tiles only and never used by a cell of the domain, read any cell
+    // of the box that lies in the domain), RS - 1 for a Dirichlet ghost (the
+    // slot after each field's box holds the Dirichlet state).  Otherwise each
+    // thread copies its cells with cp.async and loc[j][l] is the in-plane
+    // offset of the source, -1 for a Dirichlet ghost.
+    int loc[L::JH][2];
     int hring[L::JH];
 #pragma unroll
     for (int j = 0; j < L::JH; ++j) {
         const int h = tid + j * NT;
-        hoff[j][0] = hoff[j][1] = -1;
+        loc[j][0] = loc[j][1] = TMA ? RS - 1 : -1;
         hring[j] = (h / HW) * HX + h % HW;
         if (h < NH) {
             const int mx = map_coord(x0 - 2 + h % HW, nx, G.bc_lo[0], G.bc_hi[0]);
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 const int my = map_coord(y0 - 2 + 2 * (h / HW) + l, ny, G.bc_lo[1], G.bc_hi[1]);
-                if (mx >= 0 && my >= 0) hoff[j][l] = my * nx + mx;
+                if (mx < 0 || my < 0) continue;
+                if constexpr (TMA) {
+                    const int bx = min(max(mx - (x0 - 4), 0), BXW - 1);
+                    const int by = min(max(my - (y0 - 2), 0), BH - 1);
+                    loc[j][l] = by * BXW + bx;
+                } else {
+                    loc[j][l] = my * nx + mx;
+                }
             }
         }
     }
@@ -155,46 +186,119 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     const bool nf_x_edge = x0 == 0 && G.bc_lo[0] == BC_NOFLUX;
     const bool nf_y_edge = y0 == 0 && G.bc_lo[1] == BC_NOFLUX;
 
-    // ---- A: plane z -> staging (asynchronous copies; ghosts written directly).
-    // The thread that copies a pair cell is the one that converts it.
-    // lane-planar: consecutive threads copy to consecutive words (no bank conflicts)
-    T* sR = reinterpret_cast<T*>(smem + L::OFF_R);   // [field][lane][h]
-    T* sO = reinterpret_cast<T*>(smem + L::OFF_O);   // [field][lane][tid]
-    auto fetch_plane = [&](int z) {
-        const int mz = map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]);
+    // ---- A: plane z -> staging.
+    // TMA: thread 0 issues the box of each field and the own-state boxes on one
+    // mbarrier; every thread waits for its phase (bounded).  A Dirichlet ghost
+    // plane is not copied: every thread writes the Dirichlet state where its
+    // cells read.  Staging [field][RS]: the box (rows of BXW), then the slot
+    // holding the Dirichlet state.
+    // cp.async: each thread copies the cells it converts, lane-planar
+    // ([field][lane][h]: consecutive threads write consecutive words), the own
+    // state [field][lane][tid]; Dirichlet ghosts are written directly.
+    T* sR = reinterpret_cast<T*>(smem + L::OFF_R);
+    T* sO = reinterpret_cast<T*>(smem + L::OFF_O);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+    unsigned phase = 0;        // parity of the mbarrier phase waited for next
+    bool timed_out = false;    // a wait ran out: no further arrivals, copies or waits
+    unsigned stuck = 0;        // the parity of the phase that did not complete
+    if constexpr (TMA) {
+        if (tid == 0) mbar_init(bar, 1);
+        if (tid < 3) sR[tid * RS + RS - 1] = tid == 0 ? G.dir_phi : (tid == 1 ? G.dir_c : G.dir_d);
+        __syncthreads();
+    }
+    constexpr unsigned HALO_TX = 3u * BOX * sizeof(T);
+    constexpr unsigned OWN_TX = (sizeof(T) == 4 ? 3u : 2u) * BOX * sizeof(T);
+    // plane z into the staging slot (if plane), own state of plane zown (if >= 0)
+    auto fetch = [&](int z, bool plane, int zown) {
+        const int mz = plane ? map_coord(z, nz, G.bc_lo[2], G.bc_hi[2]) : 0;
+        const bool copy_plane = plane && mz != DIR_GHOST;
+        if constexpr (TMA) {
+            if (plane && !copy_plane) {
 #pragma unroll
-        for (int j = 0; j < L::JH; ++j) {
-            const int h = tid + j * NT;
-            if ((j + 1) * NT > NH && h >= NH) break;
+                for (int j = 0; j < L::JH; ++j) {
+                    if ((j + 1) * NT > NH && tid + j * NT >= NH) break;
 #pragma unroll
-            for (int l = 0; l < 2; ++l) {
-                T* dst = sR + l * NHP + h;
-                if (mz != DIR_GHOST && hoff[j][l] >= 0) {
-                    const long long gi = (long long)mz * sz + hoff[j][l];
-                    cp_async(dst, phi_in + gi);
-                    cp_async(dst + 2 * NHP, c_in + gi);
-                    cp_async(dst + 4 * NHP, d_in + gi);
-                } else {
-                    dst[0] = G.dir_phi;
-                    dst[2 * NHP] = G.dir_c;
-                    dst[4 * NHP] = G.dir_d;
+                    for (int l = 0; l < 2; ++l) {
+                        sR[loc[j][l]] = G.dir_phi;
+                        sR[RS + loc[j][l]] = G.dir_c;
+                        sR[2 * RS + loc[j][l]] = G.dir_d;
+                    }
+                }
+                fence_proxy_async_smem();   // before later TMA writes to the same slots
+            }
+            if (tid == 0 && !timed_out) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect(bar, (copy_plane ? HALO_TX : 0u) + (zown >= 0 ? OWN_TX : 0u));
+                if (!(flags & 2)) {   // flags bit 1: copies left out (a test of the bounded wait)
+                    if (copy_plane) {
+                        tma_load_3d(sR, &tm_phi, x0 - 4, y0 - 2, mz + zpad, bar);
+                        tma_load_3d(sR + RS, &tm_c, x0 - 4, y0 - 2, mz + zpad, bar);
+                        tma_load_3d(sR + 2 * RS, &tm_d, x0 - 4, y0 - 2, mz + zpad, bar);
+                    }
+                    if (zown >= 0) {
+                        tma_load_3d(sO, &tm_c, x0 - 4, y0 - 2, zown + zpad, bar);
+                        tma_load_3d(sO + RS, &tm_d, x0 - 4, y0 - 2, zown + zpad, bar);
+                        if constexpr (sizeof(T) == 4)
+                            tma_load_3d(sO + 2 * RS, &tm_clo, x0 - 4, y0 - 2, zown + zpad, bar);
+                    }
                 }
             }
+        } else {
+            if (plane) {
+#pragma unroll
+                for (int j = 0; j < L::JH; ++j) {
+                    const int h = tid + j * NT;
+                    if ((j + 1) * NT > NH && h >= NH) break;
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        T* dst = sR + l * NHP + h;
+                        if (copy_plane && loc[j][l] >= 0) {
+                            const long long gi = (long long)mz * sz + loc[j][l];
+                            cp_async(dst, phi_in + gi);
+                            cp_async(dst + 2 * NHP, c_in + gi);
+                            cp_async(dst + 4 * NHP, d_in + gi);
+                        } else {
+                            dst[0] = G.dir_phi;
+                            dst[2 * NHP] = G.dir_c;
+                            dst[4 * NHP] = G.dir_d;
+                        }
+                    }
+                }
+            }
+            if (zown >= 0) {
+                const long long gi = (long long)zown * sz + own_xy;
+                T* dst = sO + tid;
+                if (in_lo) {
+                    cp_async(dst, c_in + gi);
+                    cp_async(dst + 2 * NT, d_in + gi);
+                    if constexpr (sizeof(T) == 4) cp_async(dst + 4 * NT, clo_in + gi);
+                }
+                if (in_hi) {
+                    cp_async(dst + NT, c_in + gi + nx);
+                    cp_async(dst + 3 * NT, d_in + gi + nx);
+                    if constexpr (sizeof(T) == 4) cp_async(dst + 5 * NT, clo_in + gi + nx);
+                }
+            }
+            cp_async_commit();
         }
     };
-    auto fetch_own = [&](int z) {
-        const long long gi = (long long)z * sz + own_xy;
-        T* dst = sO + tid;
-        if (in_lo) {
-            cp_async(dst, c_in + gi);
-            cp_async(dst + 2 * NT, d_in + gi);
-            if constexpr (sizeof(T) == 4) cp_async(dst + 4 * NT, clo_in + gi);
+    // wait for the last fetch
+    auto fetched = [&]() {
+        if constexpr (TMA) {
+            if (!timed_out && !mbar_wait_bounded(bar, phase)) {
+                timed_out = true;
+                stuck = phase;
+                if (err) atomicOr(err, 1);
+            }
+            phase ^= 1u;
+        } else {
+            cp_async_wait_all();
         }
-        if (in_hi) {
-            cp_async(dst + NT, c_in + gi + nx);
-            cp_async(dst + 3 * NT, d_in + gi + nx);
-            if constexpr (sizeof(T) == 4) cp_async(dst + 5 * NT, clo_in + gi + nx);
-        }
+    };
+    // own state of the plane being updated: rows y and y+1 of the thread's pair
+    auto own_state = [&](int f, int l) -> T {
+        if constexpr (TMA) return sO[f * RS + (2 * ty + l + 2) * BXW + tx + 4];
+        else return sO[(2 * f + l) * NT + tid];
     };
     // staged plane z into the rings
     auto store_plane = [&](int oa, int oc) {
@@ -206,9 +310,16 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         for (int j = 0; j < L::JH; ++j) {
             const int hl = tid + j * NT;
             if ((j + 1) * NT > NH && hl >= NH) break;
-            const V f = vpair(sR[hl], sR[NHP + hl]);
-            const V c = vpair(sR[2 * NHP + hl], sR[3 * NHP + hl]);
-            const V d = vpair(sR[4 * NHP + hl], sR[5 * NHP + hl]);
+            V f, c, d;
+            if constexpr (TMA) {
+                f = vpair(sR[loc[j][0]], sR[loc[j][1]]);
+                c = vpair(sR[RS + loc[j][0]], sR[RS + loc[j][1]]);
+                d = vpair(sR[2 * RS + loc[j][0]], sR[2 * RS + loc[j][1]]);
+            } else {
+                f = vpair(sR[hl], sR[NHP + hl]);
+                c = vpair(sR[2 * NHP + hl], sR[3 * NHP + hl]);
+                d = vpair(sR[4 * NHP + hl], sR[5 * NHP + hl]);
+            }
             const int h = hring[j];
             const V p = vp_of<AI, STD>(K, f);
             const V cs = vfma(vsub(vlit<V>(1.0), p), d, c);
@@ -463,22 +574,19 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     // z face (z0-1, z0).  The single staging slot is refilled only after a
     // barrier has ordered every read of it.
     for (int z = z0 - 2; z <= z0; ++z) {
-        fetch_plane(z);
-        cp_async_commit();
-        cp_async_wait_all();
+        fetch(z, true, -1);
+        fetched();
         store_plane(offA(z), offC(z));
         __syncthreads();
     }
     rates_plane(z0 - 1);
-    fetch_plane(z0 + 1);
-    cp_async_commit();
-    cp_async_wait_all();
+    fetch(z0 + 1, true, -1);
+    fetched();
     __syncthreads();   // plane z0+1 reuses the {c_s, c_l} / phi slots of z0-2
     store_plane(offA(z0 + 1), offC(z0 + 1));
     __syncthreads();
     rates_plane(z0);
-    fetch_plane(z0 + 2);
-    cp_async_commit();
+    fetch(z0 + 2, true, -1);
     V fzc_down, fzd_down;
     zface(z0 - 1, own_h, own_r, fzc_down, fzd_down);
     if (z_noflux(z0 - 1)) fzc_down = fzd_down = vpair(T(0), T(0));
@@ -504,7 +612,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const T bc_ = below.x, bd_ = below.y;
         const V dFc = vadd(vadd(vsub(fxc, left.a), vpair(fyc.x - bc_, fyc.y - fyc.x)), vsub(fzc, fzc_down));
         const V dFd = vadd(vadd(vsub(fxd, left.b), vpair(fyd.x - bd_, fyd.y - fyd.x)), vsub(fzd, fzd_down));
-        const V c_k = vpair(sO[tid], sO[NT + tid]), d_k = vpair(sO[2 * NT + tid], sO[3 * NT + tid]);
+        const V c_k = vpair(own_state(0, 0), own_state(0, 1)), d_k = vpair(own_state(1, 0), own_state(1, 1));
         V phi_new;
         if constexpr (sizeof(T) == 4) phi_new = vfma(K.dt_dx2, rate_prev, phi_prev);
         else phi_new = vfma(K.dt_dx2, sD[rd_p1 + own_r], sA[ra_m1 + own_h].a);
@@ -513,7 +621,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         V c_new, lo_new;
         if constexpr (sizeof(T) == 4) {
             // compensated (TwoSum) update of c = hi + lo
-            const V lo_k = vpair(sO[4 * NT + tid], sO[5 * NT + tid]);
+            const V lo_k = vpair(own_state(2, 0), own_state(2, 1));
             const V s_ = vadd(c_k, dcv);
             const V bv = vsub(s_, c_k);
             const V err = vadd(vsub(c_k, vsub(s_, bv)), vsub(dcv, bv));
@@ -546,13 +654,11 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     //   2: copies of plane k+3 and of the own state of k in flight | rates of
     //      plane k+1 (a thread's faces read only its own new rate) | faces of k
     for (int k = z0; k < z1; ++k) {
-        cp_async_wait_all();
+        fetched();
         if (k > z0) update(k - 1);
         store_plane(ra_p2, rc_p2);
         __syncthreads();
-        if (k + 1 < z1) fetch_plane(k + 3);
-        fetch_own(k);
-        cp_async_commit();
+        fetch(k + 3, k + 1 < z1, k);
         const bool ghost_up = ghost(k + 1);
         if constexpr (sizeof(T) == 4) {
             // The own rate of plane k+1 goes to the z face in a register and to
@@ -603,8 +709,12 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         const int td = rd_0;
         rd_0 = rd_p1; rd_p1 = td;
     }
-    cp_async_wait_all();
+    fetched();
     update(z1 - 1);
+    // a wait that ran out: give copies still in flight a bounded time to land
+    // before the CTA's shared memory is released
+    if constexpr (TMA)
+        if (tid == 0 && timed_out) mbar_wait_bounded(bar, stuck);
 }
 
 // planes per CTA: minimise (waves of resident CTAs) x (planes + prologue) over
@@ -625,6 +735,25 @@ static int choose_zchunk(long long tiles, int nz, long long resident) {
     return best;
 }
 
+template <typename T>
+using Step3dKernel = decltype(&step3d_kernel<T, 32, 16, true, true, false, false>);
+
+// the instances: [default physics][19-point Laplacian][a != 0], staged by TMA
+// (FP32 only) or by per-cell copies
+template <typename T, bool TMA>
+static void step3d_table(Step3dKernel<T> k[2][2][2]) {
+    constexpr int TX = 32, TY = 16;
+    constexpr bool M = TMA && sizeof(T) == 4;
+    k[0][0][0] = step3d_kernel<T, TX, TY, false, false, false, M>;
+    k[0][0][1] = step3d_kernel<T, TX, TY, false, true, false, M>;
+    k[0][1][0] = step3d_kernel<T, TX, TY, true, false, false, M>;
+    k[0][1][1] = step3d_kernel<T, TX, TY, true, true, false, M>;
+    k[1][0][0] = step3d_kernel<T, TX, TY, false, false, true, M>;
+    k[1][0][1] = step3d_kernel<T, TX, TY, false, true, true, M>;
+    k[1][1][0] = step3d_kernel<T, TX, TY, true, false, true, M>;
+    k[1][1][1] = step3d_kernel<T, TX, TY, true, true, true, M>;
+}
+
 // kernel attributes (once per device) and the occupancy the z-chunking plans with
 template <typename T>
 static cudaError_t step3d_setup(int* per_sm, int* sms) {
@@ -637,17 +766,16 @@ static cudaError_t step3d_setup(int* per_sm, int* sms) {
     if (dev < 0 || dev >= DeviceSetup::MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(setup.mu);
     if (!setup.done[dev]) {
-        decltype(&step3d_kernel<T, TX, TY, true, true, false>) kerns[8] = {
-            step3d_kernel<T, TX, TY, false, false, false>, step3d_kernel<T, TX, TY, false, true, false>,
-            step3d_kernel<T, TX, TY, true, false, false>, step3d_kernel<T, TX, TY, true, true, false>,
-            step3d_kernel<T, TX, TY, false, false, true>, step3d_kernel<T, TX, TY, false, true, true>,
-            step3d_kernel<T, TX, TY, true, false, true>, step3d_kernel<T, TX, TY, true, true, true>};
-        for (int i = 0; i < 8 && e == cudaSuccess; ++i)
-            e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+        Step3dKernel<T> kt[2][2][2][2];
+        step3d_table<T, false>(kt[0]);
+        step3d_table<T, true>(kt[1]);
+        for (int i = 0; i < 16 && e == cudaSuccess; ++i)
+            e = cudaFuncSetAttribute((&kt[0][0][0][0])[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)L::BYTES);
         if (e != cudaSuccess) return e;
         int s = 1, p = 1;
         cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kerns[7], L::NT, L::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kt[0][1][1][1], L::NT, L::BYTES);
         setup.sms[dev] = s;
         setup.per_sm[dev] = p < 1 ? 1 : p;
         setup.done[dev] = true;
@@ -677,11 +805,6 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     // 19- or 7-point Laplacian x shape parameter a != 0 or a = 0
     // 19- or 7-point Laplacian x shape parameter a != 0 or a = 0 x default physics
     // (quintic h, M_i = D_i c_i: literal coefficients) or not
-    decltype(&step3d_kernel<T, TX, TY, true, true, false>) kerns[2][2][2] = {
-        {{step3d_kernel<T, TX, TY, false, false, false>, step3d_kernel<T, TX, TY, false, true, false>},
-         {step3d_kernel<T, TX, TY, true, false, false>, step3d_kernel<T, TX, TY, true, true, false>}},
-        {{step3d_kernel<T, TX, TY, false, false, true>, step3d_kernel<T, TX, TY, false, true, true>},
-         {step3d_kernel<T, TX, TY, true, false, true>, step3d_kernel<T, TX, TY, true, true, true>}}};
     const HostProblem& P = *a.prob;
     int zchunk = 0, nchunks = 0;
     cudaError_t e = step3d_chunks<T>(P, a.zchunk, &zchunk, &nchunks);
@@ -695,13 +818,78 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     const int count = a.zcount > 0 ? std::min(a.zcount, nchunks - zfirst) : nchunks;
     if (count <= 0) return cudaSuccess;
     grid.z = count;
+    // TMA plane loads (FP32): one tensor map per state word over planes -zpad
+    // .. nz - 1 + zpad (a slab's arrays hold two ghost planes beyond each z
+    // side) with the staging box.  Rows must be whole multiples of 16 bytes,
+    // and a periodic x or y side, whose ghosts come from outside the box, takes
+    // per-cell copies.
+    CUtensorMap maps[4];
+    std::memset(maps, 0, sizeof(maps));
+    int flags = 0;
+    const int zpad = (P.bc_lo[2] == PF_BC_HALO || P.bc_hi[2] == PF_BC_HALO) ? 2 : 0;
+    const bool periodic_xy = P.bc_lo[0] == PF_BC_PERIODIC || P.bc_hi[0] == PF_BC_PERIODIC ||
+                             P.bc_lo[1] == PF_BC_PERIODIC || P.bc_hi[1] == PF_BC_PERIODIC;
+    if (sizeof(T) == 4 && !a.no_tma && !periodic_xy && (P.n[0] * sizeof(T)) % 16 == 0) {
+        const uint64_t n[3] = {(uint64_t)P.n[0], (uint64_t)P.n[1], (uint64_t)P.n[2] + 2 * zpad};
+        const uint32_t box[3] = {(uint32_t)L::BXW, (uint32_t)L::BH, 1};
+        const size_t plane = (size_t)P.n[0] * P.n[1] * sizeof(T);
+        const void* src[4] = {a.phi_in, a.c_in, a.d_in, a.clo_in};
+        bool ok = true;
+        for (int f = 0; f < (sizeof(T) == 4 ? 4 : 3) && ok; ++f) {
+            const char* base = static_cast<const char*>(src[f]) - zpad * plane;
+            ok = reinterpret_cast<uintptr_t>(base) % 16 == 0 &&
+                 encode_tensor_map_3d(&maps[f], sizeof(T) == 8, base, n, box);
+        }
+        if (ok) flags |= 1;
+    }
+    if (a.drop_copies) flags |= 2;
+    Step3dKernel<T> kt[2][2][2];
+    if (flags & 1) step3d_table<T, true>(kt);
+    else step3d_table<T, false>(kt);
     const bool std_phys = P.interp == 0 && P.mobility == 0;
-    auto kern = kerns[std_phys ? 1 : 0][C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
+    auto kern = kt[std_phys ? 1 : 0][C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
     kern<<<grid, block, L::BYTES, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
-        static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk, zfirst);
+        static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk, zfirst, maps[0], maps[1], maps[2],
+        maps[3], flags, zpad, a.err);
     return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled, looked up from the driver once per process
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+bool encode_tensor_map_3d(CUtensorMap* map, bool fp64, const void* base, const uint64_t n[3],
+                          const uint32_t box[3]) {
+    EncodeTiledFn fn = encoder();
+    if (!fn) return false;
+    const size_t es = fp64 ? 8 : 4;
+    const cuuint64_t dims[3] = {n[0], n[1], n[2]};
+    const cuuint64_t strides[2] = {n[0] * es, n[0] * n[1] * es};
+    const cuuint32_t bdim[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              const_cast<void*>(base), dims, strides, bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template cudaError_t launch_step3d<float>(const StepLaunch&, const Consts<float>&, const Clock<float>&);

@@ -1,0 +1,87 @@
+// pf_tma.cuh -- tensor-memory-accelerator (TMA) plane loads for the 3D step:
+// a tiled 3D box copied from global to shared memory by cp.async.bulk.tensor,
+// its completion counted on a shared-memory mbarrier, and waits on that
+// barrier bounded in time (a wait that runs out records an error instead of
+// spinning forever).  Host side: the tensor-map encoder, looked up from the
+// driver once per process.
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace pf {
+
+// limit of one mbarrier wait, in nanoseconds of the global timer
+constexpr unsigned long long TMA_WAIT_NS = 500000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one arrival that also expects `bytes` of transactions in the current phase
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete; false if it has not
+// completed within TMA_WAIT_NS (or 2^26 polls).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > TMA_WAIT_NS) return false;
+    }
+    return false;
+}
+
+// order earlier generic-proxy accesses of shared memory before later
+// asynchronous-proxy writes to it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// box of `map` at element coordinates (x, y, z) into shared memory at dst
+// (128-byte aligned), completion counted on bar.  x times the element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Host: encode a tiled 3D tensor map of n[0] x n[1] x n[2] elements (x
+// fastest, dense) at base with the box dimensions box[3]; false if the driver
+// entry point is missing or the encoder rejects the description.
+bool encode_tensor_map_3d(CUtensorMap* map, bool fp64, const void* base, const uint64_t n[3],
+                          const uint32_t box[3]);
+
+}  // namespace pf
