@@ -74,10 +74,15 @@ struct PTile {
     static constexpr int RS = BOX + 128 / (int)sizeof(T);
     static constexpr int NHP = (NH + 15) / 16 * 16;
     static constexpr size_t OFF_R = (OFF_FY + sizeof(V) * (TYP + 1) * TX + 127) / 128 * 128;   // phi, c, d
-    static constexpr size_t OFF_O = OFF_R + sizeof(T) * (3 * RS > 6 * NHP ? 3 * RS : 6 * NHP);   // c, d, c_lo
-    static constexpr size_t OFF_BAR = OFF_O + sizeof(T) * (3 * RS > 6 * NT ? 3 * RS : 6 * NT);   // mbarrier
+    static constexpr size_t OFF_O = OFF_R + sizeof(T) * 3 * RS;                               // c, d, c_lo
+    static constexpr size_t OFF_BAR = OFF_O + sizeof(T) * 3 * RS;                             // mbarrier
     static constexpr size_t BYTES = OFF_BAR + 16;
     static_assert((sizeof(T) * RS) % 128 == 0 && OFF_BAR % 8 == 0, "staging boxes 128-byte aligned");
+    // the per-cell layout needs less: the rest of the SM's 228 KB stays L1,
+    // which its cp.async copies pass through
+    static constexpr size_t OFF_R_CP = OFF_FY + sizeof(V) * (TYP + 1) * TX;
+    static constexpr size_t OFF_O_CP = OFF_R_CP + sizeof(T) * 6 * NHP;
+    static constexpr size_t BYTES_CP = OFF_O_CP + sizeof(T) * 6 * NT;
     static constexpr int NB = NR - NT;   // ring cells besides the threads' own pairs
     static_assert(NB == 2 * RW + 2 * TYP && NB <= NT, "ring = own pairs + border");
 };
@@ -195,8 +200,8 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     // cp.async: each thread copies the cells it converts, lane-planar
     // ([field][lane][h]: consecutive threads write consecutive words), the own
     // state [field][lane][tid]; Dirichlet ghosts are written directly.
-    T* sR = reinterpret_cast<T*>(smem + L::OFF_R);
-    T* sO = reinterpret_cast<T*>(smem + L::OFF_O);
+    T* sR = reinterpret_cast<T*>(smem + (TMA ? L::OFF_R : L::OFF_R_CP));
+    T* sO = reinterpret_cast<T*>(smem + (TMA ? L::OFF_O : L::OFF_O_CP));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
     unsigned phase = 0;        // parity of the mbarrier phase waited for next
     bool timed_out = false;    // a wait ran out: no further arrivals, copies or waits
@@ -769,13 +774,17 @@ static cudaError_t step3d_setup(int* per_sm, int* sms) {
         Step3dKernel<T> kt[2][2][2][2];
         step3d_table<T, false>(kt[0]);
         step3d_table<T, true>(kt[1]);
+        // per-cell instances first: in FP64 the TMA table holds the same
+        // functions, which then keep the larger limit
         for (int i = 0; i < 16 && e == cudaSuccess; ++i)
             e = cudaFuncSetAttribute((&kt[0][0][0][0])[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)L::BYTES);
+                                     (int)(i < 8 ? L::BYTES_CP : L::BYTES));
         if (e != cudaSuccess) return e;
-        int s = 1, p = 1;
+        int s = 1, p = 1, q = 1;
         cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kt[0][1][1][1], L::NT, L::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kt[0][1][1][1], L::NT, L::BYTES_CP);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, kt[1][1][1][1], L::NT, L::BYTES);
+        p = std::min(p, q);
         setup.sms[dev] = s;
         setup.per_sm[dev] = p < 1 ? 1 : p;
         setup.done[dev] = true;
@@ -848,7 +857,7 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     else step3d_table<T, false>(kt);
     const bool std_phys = P.interp == 0 && P.mobility == 0;
     auto kern = kt[std_phys ? 1 : 0][C.lap == 19 ? 1 : 0][P.a != 0.0 ? 1 : 0];
-    kern<<<grid, block, L::BYTES, a.stream>>>(
+    kern<<<grid, block, (flags & 1) ? L::BYTES : L::BYTES_CP, a.stream>>>(
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
         static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk, zfirst, maps[0], maps[1], maps[2],
