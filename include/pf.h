@@ -193,8 +193,12 @@ int pf_step(pf_handle* h, int64_t n);
  * stream, and the first step of each chunk starts, on further internal
  * streams, as soon as the planes it reads (two below, one above the chunk,
  * wrapped on a periodic z axis) are in, so that stepping overlaps the
- * transfer.  The handle's stream waits for all of it; the remaining n - 1
- * steps follow on it.  Returns once the host buffers have been read (the
+ * transfer.  From page-locked host memory the slabs are first copied by the
+ * copy engine into a device staging buffer; those copies wait only for the
+ * previous call's conversion of the same slab, not for its steps, so that
+ * back-to-back calls keep the host link busy.  The handle's stream waits for
+ * all of it; the remaining n - 1 steps follow on it.  Returns once the host
+ * buffers have been read (the
  * caller may reuse them); the steps may still be running.  Other grids,
  * pageable host memory or n = 0: the two calls in sequence.  The handle
  * creates its internal streams and events on first use and frees them in

@@ -442,7 +442,6 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
     if (e != cudaSuccess) return cuda_fail(h, e, "device query");
     if (e == cudaSuccess) e = cudaEventRecord(start, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(conv, start, 0);
-    if (e == cudaSuccess && ce) e = cudaStreamWaitEvent(h->up_cp, start, 0);
     for (int j = 0; j < nch && e == cudaSuccess; ++j) {
         const long long z0 = (long long)j * zchunk, z1 = std::min<long long>(nz, z0 + zchunk);
         const void* from[3] = {src[0], src[1], src[2]};
@@ -450,6 +449,11 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
             // the slab's three fields by the copy engine, then converted from
             // device memory once they are in
             const size_t off = (size_t)(z0 * plane) * elem, len = (size_t)((z1 - z0) * plane) * elem;
+            // the staging slab is free once the previous call's conversion of
+            // it is done (its event, not yet re-recorded by this call); the
+            // copies need not wait for the previous step, which the
+            // conversion below does wait for
+            e = cudaStreamWaitEvent(h->up_cp, h->ov_ev[j], 0);
             for (int f = 0; f < 3 && e == cudaSuccess; ++f)
                 e = cudaMemcpyAsync(static_cast<char*>(h->up_stage[f]) + off, static_cast<const char*>(host[f]) + off,
                                     len, cudaMemcpyHostToDevice, h->up_cp);
