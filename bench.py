@@ -909,7 +909,9 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for i in range(ke):
-            sim.set_fields_step(*host_views, n=1)          # upload overlapped with the step
+            # upload overlapped with the step; the inputs stay unchanged, so the
+            # call need not wait for its copies (the next one is queued at once)
+            sim.set_fields_step(*host_views, n=1, wait=False)
             sim.get_fields_async(out_host=back[i % 2])     # the stepped fields, to the host
         sim.sync()
         e2e_s = time.perf_counter() - t0

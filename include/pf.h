@@ -54,7 +54,9 @@ enum {
 };
 enum { PF_BC_NOFLUX = 0, PF_BC_PERIODIC = 1, PF_BC_DIRICHLET = 2, PF_BC_HALO = 3 };
 enum { PF_FP32 = 0, PF_FP64 = 1 };
-enum { PF_HOST = 0, PF_DEVICE = 1 };
+enum { PF_HOST = 0, PF_DEVICE = 1,
+       /* pf_set_fields_step only: page-locked host memory read without a wait */
+       PF_HOST_ASYNC = 2 };
 enum { PF_INTERP_QUINTIC = 0, PF_INTERP_CUBIC = 1 };  /* h(phi), Sec. "Choice of interpolation functions" */
 enum { PF_MOBILITY_DC = 0, PF_MOBILITY_CONST = 1 };   /* M_i = D_i c_i  or  M_i = D_i */
 
@@ -158,8 +160,10 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where);
  * after the work already queued on the handle's stream: into device memory
  * (where = PF_DEVICE) directly, or into page-locked host memory (PF_HOST;
  * pageable memory returns PF_EINVAL) through a device staging buffer of the
- * handle's and the copy engine (the staging buffer, 3 n[0]*n[1]*n[2] values,
- * is allocated on the first such call; PF_ENOMEM if that fails);
+ * handle's and the copy engine (two staging sets of 3 n[0]*n[1]*n[2] values,
+ * used in turn so that a read-back's conversion need not wait for the
+ * previous one's host copies, each allocated on first use; PF_ENOMEM if that
+ * fails);
  * n[0]*n[1]*n[2] values each of the handle's precision.  The values are valid after pf_sync.
  * The handle keeps the state being read intact until the read-back has read
  * it: every later call that writes the state first orders itself after that
@@ -197,8 +201,12 @@ int pf_step(pf_handle* h, int64_t n);
  * copy engine into a device staging buffer; those copies wait only for the
  * previous call's conversion of the same slab, not for its steps, so that
  * back-to-back calls keep the host link busy.  The handle's stream waits for
- * all of it; the remaining n - 1 steps follow on it.  Returns once the host
- * buffers have been read (the
+ * all of it; the remaining n - 1 steps follow on it.  where = PF_HOST_ASYNC:
+ * page-locked host memory (PF_EINVAL otherwise) that the call does not wait
+ * for; the caller keeps the buffers unchanged until pf_sync, or any other
+ * call that synchronises the handle's stream, returns, so that a pipeline of
+ * uploads and read-backs is queued without host round trips.  PF_HOST: returns
+ * once the host buffers have been read (the
  * caller may reuse them); the steps may still be running.  Other grids,
  * pageable host memory or n = 0: the two calls in sequence.  The handle
  * creates its internal streams and events on first use and frees them in

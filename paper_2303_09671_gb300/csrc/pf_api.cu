@@ -39,7 +39,13 @@ struct pf_handle {
     // stream before it and one after the read-back; pending while no later work
     // of the handle has been ordered after it
     cudaStream_t rb = nullptr;
-    void* rb_stage[3] = {nullptr, nullptr, nullptr};   // device staging of the converted fields
+    // device staging of the converted fields, two sets used in turn, so that a
+    // read-back's conversion need not wait for the previous one's host copies;
+    // the conversions run on rb_cv, the copies on rb
+    void* rb_stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int rb_slot = 0;
+    cudaStream_t rb_cv = nullptr;
+    cudaEvent_t rb_copied[2] = {nullptr, nullptr};   // the host copies out of staging set s are done
     bool rb_copy = true;         // read-backs to host: staged + copy engine (true) or kernel-written
     // pf_set_fields_step from page-locked host memory: slabs copied by the copy
     // engine into a device staging buffer (on their own stream, one event per
@@ -300,15 +306,20 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
 
 void pf_destroy(pf_handle* h) {
     if (!h) return;
+    if (h->rb_cv) cudaStreamSynchronize(h->rb_cv);
     if (h->rb) cudaStreamSynchronize(h->rb);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     if (h->rb) cudaStreamDestroy(h->rb);
+    if (h->rb_cv) cudaStreamDestroy(h->rb_cv);
     if (h->rb_start) cudaEventDestroy(h->rb_start);
     if (h->rb_done) cudaEventDestroy(h->rb_done);
     if (h->rb_read) cudaEventDestroy(h->rb_read);
-    for (void* p : h->rb_stage)
-        if (p) cudaFree(p);
+    for (cudaEvent_t ev : h->rb_copied)
+        if (ev) cudaEventDestroy(ev);
+    for (auto& set : h->rb_stage)
+        for (void* p : set)
+            if (p) cudaFree(p);
     for (void* p : h->up_stage)
         if (p) cudaFree(p);
     if (h->up_cp) cudaStreamDestroy(h->up_cp);
@@ -360,14 +371,19 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
                        int64_t n) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
-    if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (where != PF_HOST && where != PF_DEVICE && where != PF_HOST_ASYNC)
+        return fail(h, PF_EINVAL, "where must be PF_HOST, PF_HOST_ASYNC or PF_DEVICE");
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
     if (h->halo[0] || h->halo[1])
         return fail(h, PF_EINVAL, "a slab with halo sides sets its fields, imports its halos, then steps");
+    // PF_HOST_ASYNC: page-locked host memory, the host not waiting for its copies
+    const bool no_wait = where == PF_HOST_ASYNC;
+    if (no_wait) where = PF_HOST;
     const pf::HostProblem& P = h->P;
     const void* src[3] = {phi, cs, cl};
     const void* host[3] = {phi, cs, cl};
     const bool readable = where == PF_DEVICE || device_views(src);
+    if (no_wait && !readable) return fail(h, PF_EINVAL, "PF_HOST_ASYNC needs page-locked host memory");
     int zchunk = 0, nch = 0;
     cudaError_t e = cudaSuccess;
     if (P.dim == 3 && !h->generic && n > 0 && readable) {
@@ -507,7 +523,7 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
     h->rb_pending = false;   // the handle's stream now follows the read-back too
     h->have_front = false;
     h->step += 1;
-    if (where == PF_HOST) {
+    if (where == PF_HOST && !no_wait) {
         // the caller may reuse its host memory once the last slab is read
         e = cudaEventSynchronize(ce ? h->cp_ev[nch - 1] : h->ov_ev[nch - 1]);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
@@ -526,47 +542,57 @@ int pf_get_fields_async(pf_handle* h, void* phi, void* cs, void* cl, int where) 
         if (!device_views(views)) return fail(h, PF_EINVAL, "pf_get_fields_async needs page-locked host memory");
         for (int f = 0; f < 3; ++f) tgt[f] = const_cast<void*>(views[f]);
     }
-    // host outputs converted into a staging buffer of the handle's own (the
+    // host outputs converted into a staging set of the handle's own (the
     // idle state buffer is the next upload's target), then copied by the copy
     // engine (PF_READBACK=direct: written by the conversion kernel itself)
     const bool staged = where == PF_HOST && h->rb_copy;
+    const int slot = h->rb_slot;
     if (staged) {
         for (int f = 0; f < 3; ++f) {
-            if (!h->rb_stage[f]) {
-                cudaError_t a = cudaMalloc(&h->rb_stage[f], bytes);
+            if (!h->rb_stage[slot][f]) {
+                cudaError_t a = cudaMalloc(&h->rb_stage[slot][f], bytes);
                 if (a != cudaSuccess) {
                     cudaGetLastError();
-                    h->rb_stage[f] = nullptr;
+                    h->rb_stage[slot][f] = nullptr;
                     return fail(h, PF_ENOMEM, std::string("read-back staging: ") + cudaGetErrorString(a));
                 }
             }
-            tgt[f] = h->rb_stage[f];
+            tgt[f] = h->rb_stage[slot][f];
         }
     }
     cudaError_t e = cudaSuccess;
     if (!h->rb) {
         e = cudaStreamCreateWithFlags(&h->rb, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->rb_cv, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_start, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_read, cudaEventDisableTiming);
+        for (int s2 = 0; s2 < 2 && e == cudaSuccess; ++s2)
+            e = cudaEventCreateWithFlags(&h->rb_copied[s2], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(h, e, "read-back stream");
     }
     // written by the kernel: two blocks per SM (bound by the link or DRAM, the
     // SMs left to an upload's conversion and steps); staged: the conversion
-    // on the full grid, then the copy engine
+    // on the full grid, then the copy engine.  The conversion (rb_cv) waits for
+    // the work queued on the handle's stream and, staged, for the host copies
+    // that last read its staging set; the copies (rb) follow the conversion.
     int dev = 0, nsms = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_start, h->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb_cv, h->rb_start, 0);
+    if (e == cudaSuccess && staged) e = cudaStreamWaitEvent(h->rb_cv, h->rb_copied[slot], 0);
     if (e == cudaSuccess)
-        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb, staged ? 0 : 2 * nsms);
-    if (e == cudaSuccess) e = cudaEventRecord(h->rb_read, h->rb);
+        e = pf::launch_from_state(h->P, h->buf[h->cur], tgt[0], tgt[1], tgt[2], h->rb_cv, staged ? 0 : 2 * nsms);
+    if (e == cudaSuccess) e = cudaEventRecord(h->rb_read, h->rb_cv);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb, h->rb_read, 0);
     void* out[3] = {phi, cs, cl};
     for (int f = 0; f < 3 && e == cudaSuccess && staged; ++f)
         e = cudaMemcpyAsync(out[f], tgt[f], bytes, cudaMemcpyDeviceToHost, h->rb);
+    if (e == cudaSuccess && staged) e = cudaEventRecord(h->rb_copied[slot], h->rb);
     if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->rb);
     if (e != cudaSuccess) return cuda_fail(h, e, "read-back");
+    if (staged) h->rb_slot ^= 1;
     h->rb_pending = true;
     return PF_OK;
 }

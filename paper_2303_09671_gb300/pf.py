@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ETIMEOUT, PF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-PF_HOST, PF_DEVICE = 0, 1
+PF_HOST, PF_DEVICE, PF_HOST_ASYNC = 0, 1, 2
 BC = {"noflux": 0, "periodic": 1, "dirichlet": 2, "halo": 3}
 PRECISION = {"fp32": 0, "fp64": 1}
 
@@ -219,10 +219,17 @@ class Sim:
         ptrs, where, _keep = self._field_ptrs(phi, cs, cl)
         _check(lib().pf_set_fields(self._h, *ptrs, where), self._h)
 
-    def set_fields_step(self, phi, cs, cl, n: int = 1):
+    def set_fields_step(self, phi, cs, cl, n: int = 1, wait: bool = True):
         """set_fields then step(n), the upload overlapped with the first step
-        (3D, device or page-locked host fields)."""
-        ptrs, where, _keep = self._field_ptrs(phi, cs, cl)
+        (3D, device or page-locked host fields).  wait=False (page-locked host
+        arrays of the handle's dtype, contiguous): the call returns without
+        waiting for the copies; the arrays must stay unchanged until sync() or
+        another synchronising call returns."""
+        ptrs, where, keep = self._field_ptrs(phi, cs, cl)
+        if not wait and where == PF_HOST:
+            if any(k is not a for k, a in zip(keep, (phi, cs, cl))):
+                raise ValueError("wait=False needs contiguous host arrays of the handle's dtype (no copy)")
+            where = PF_HOST_ASYNC
         _check(lib().pf_set_fields_step(self._h, *ptrs, where, int(n)), self._h)
 
     def _device_out(self, out):

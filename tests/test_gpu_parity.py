@@ -537,6 +537,18 @@ def test_get_fields_async_pipeline(precision):
         s.sync()
         for w, out in zip(want, outs):
             assert all(np.array_equal(a, o.numpy()) for a, o in zip(w, out))
+        # the same pipeline with uploads that do not wait for their copies
+        # (PF_HOST_ASYNC): the host queues everything, one wait at the end
+        outs2 = [[torch.empty(w[0].shape, dtype=tdt).pin_memory() for _ in range(3)] for w in want]
+        for st, out in zip(states, outs2):
+            s.set_clock(0, 0)
+            s.set_fields_step(*[x.numpy() for x in st], n=1, wait=False)
+            s.get_fields_async(out_host=[o.numpy() for o in out])
+        s.sync()
+        for w, out in zip(want, outs2):
+            assert all(np.array_equal(a, o.numpy()) for a, o in zip(w, out))
+        with pytest.raises(PFError, match="page-locked"):
+            s.set_fields_step(*[np.ascontiguousarray(x.numpy().copy()) for x in states[0]], n=1, wait=False)
         # a read-back then a step: the read-back sees the state before the step
         dev = [torch.empty(want[2][0].shape, dtype=tdt, device="cuda") for _ in range(3)]
         s.get_fields_async(out=dev)
