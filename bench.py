@@ -192,9 +192,28 @@ def cpu_baseline(n, max_seconds=25.0):
         el = time.perf_counter() - t0
         if el > max_seconds or steps >= 3:
             break
-    return {"value": cells * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{steps} FP64 oracle steps of the full {n}^3 grid after 1 warm-up step",
-            "seconds": el}
+    out = {"value": cells * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{steps} FP64 oracle steps of the full {n}^3 grid after 1 warm-up step",
+           "seconds": el}
+    # one host thread on a 64^3 grid of the same recipe (seed radius scaled to the box)
+    all_threads = oracle.num_threads()
+    try:
+        oracle.set_threads(1)
+        pr1, phi1, cs1, cl1 = wl.sphere_seed_3d(n=64, radius_cells=5.0, **PARAMS)
+        st1 = oracle.State(pr1, phi1, cs1, cl1)
+        st1.step(1)
+        s1, t1 = 0, time.perf_counter()
+        while True:
+            st1.step(1)
+            s1 += 1
+            el1 = time.perf_counter() - t1
+            if el1 > 2.0 or s1 >= 5:
+                break
+        out["single_thread_64"] = {"value": 64 ** 3 * s1 / el1, "unit": UNIT, "cores": 1,
+                                   "sample": f"{s1} FP64 oracle steps of a 64^3 sphere seed, one thread"}
+    finally:
+        oracle.set_threads(all_threads)
+    return out
 
 
 def sm_count(device=0):

@@ -123,12 +123,19 @@ def lib():
             L.orc_front.argtypes = [P, C, dp, dp, dp, dp, dp]
             L.orc_mixture.argtypes = [P, dp, dp, dp, ctypes.c_int64, dp, dp]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_threads.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's later sweeps; returns the count in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _params(p: dict) -> _Params:

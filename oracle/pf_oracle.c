@@ -44,6 +44,18 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following sweeps (n <= 0: leave unchanged); returns the
+ * number in use afterwards. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ---------------------------------------------------------------- pointwise */
 
 /* h(phi): quintic or cubic (Sec. "Choice of interpolation functions") */

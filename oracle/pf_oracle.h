@@ -94,6 +94,7 @@ int orc_front(const orc_params* P, const orc_clock* clk, const double* phi,
               double* c_max);
 
 int orc_num_threads(void);
+int orc_set_threads(int n);   /* threads of later sweeps (n <= 0: unchanged); returns the count */
 
 #ifdef __cplusplus
 }
