@@ -76,7 +76,10 @@ struct PTile {
     static constexpr size_t OFF_R = (OFF_FY + sizeof(V) * (TYP + 1) * TX + 127) / 128 * 128;   // phi, c, d
     static constexpr size_t OFF_O = OFF_R + sizeof(T) * 3 * RS;                               // c, d, c_lo
     static constexpr size_t OFF_BAR = OFF_O + sizeof(T) * 3 * RS;                             // mbarrier
-    static constexpr size_t BYTES = OFF_BAR + 16;
+    // the updated plane of the tile (phi, c, d, c_lo: TX x TY each), written
+    // back by TMA box stores
+    static constexpr size_t OFF_W = (OFF_BAR + 16 + 127) / 128 * 128;
+    static constexpr size_t BYTES = OFF_W + sizeof(T) * 4 * TX * TY;
     static_assert((sizeof(T) * RS) % 128 == 0 && OFF_BAR % 8 == 0, "staging boxes 128-byte aligned");
     // the per-cell layout needs less: the rest of the SM's 228 KB stays L1,
     // which its cp.async copies pass through
@@ -96,7 +99,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
               T* __restrict__ d_out, T* __restrict__ clo_out, const PairConsts<typename Lanes<T>::V> K,
               const GridConsts<T> G, int zchunk, int zbase, const __grid_constant__ CUtensorMap tm_phi,
               const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_d,
-              const __grid_constant__ CUtensorMap tm_clo, int flags, int zpad, int* __restrict__ err) {
+              const __grid_constant__ CUtensorMap tm_clo, const __grid_constant__ CUtensorMap tw_phi,
+              const __grid_constant__ CUtensorMap tw_c, const __grid_constant__ CUtensorMap tw_d,
+              const __grid_constant__ CUtensorMap tw_clo, int flags, int zpad, int* __restrict__ err) {
     using L = PTile<T, TX, TY>;
     using V = typename L::V;
     using Q = typename L::Q;
@@ -203,6 +208,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     T* sR = reinterpret_cast<T*>(smem + (TMA ? L::OFF_R : L::OFF_R_CP));
     T* sO = reinterpret_cast<T*>(smem + (TMA ? L::OFF_O : L::OFF_O_CP));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+    T* sW = reinterpret_cast<T*>(smem + L::OFF_W);   // [field][TY][TX]: the updated plane
     unsigned phase = 0;        // parity of the mbarrier phase waited for next
     bool timed_out = false;    // a wait ran out: no further arrivals, copies or waits
     unsigned stuck = 0;        // the parity of the phase that did not complete
@@ -637,21 +643,50 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             c_new = vadd(c_k, dcv);
             lo_new = c_new;
         }
-        const long long gi = (long long)k * sz + own_xy;
-        if (in_lo) {
-            phi_out[gi] = phi_new.x;
-            c_out[gi] = c_new.x;
-            d_out[gi] = d_new.x;
-            if constexpr (sizeof(T) == 4) clo_out[gi] = lo_new.x;
-        }
-        if (in_hi) {
-            phi_out[gi + nx] = phi_new.y;
-            c_out[gi + nx] = c_new.y;
-            d_out[gi + nx] = d_new.y;
-            if constexpr (sizeof(T) == 4) clo_out[gi + nx] = lo_new.y;
+        if constexpr (TMA) {
+            // into the out tile (rows y, y+1 of the pair); thread 0 stores the
+            // tile's boxes after the next barrier (cells outside the grid are
+            // clipped by the store)
+            T* w = sW + (2 * ty) * TX + tx;
+            w[0] = phi_new.x;
+            w[TX] = phi_new.y;
+            w[TX * TY] = c_new.x;
+            w[TX * TY + TX] = c_new.y;
+            w[2 * TX * TY] = d_new.x;
+            w[2 * TX * TY + TX] = d_new.y;
+            w[3 * TX * TY] = lo_new.x;
+            w[3 * TX * TY + TX] = lo_new.y;
+            fence_proxy_async_smem();   // before the asynchronous proxy reads the tile
+        } else {
+            const long long gi = (long long)k * sz + own_xy;
+            if (in_lo) {
+                phi_out[gi] = phi_new.x;
+                c_out[gi] = c_new.x;
+                d_out[gi] = d_new.x;
+                if constexpr (sizeof(T) == 4) clo_out[gi] = lo_new.x;
+            }
+            if (in_hi) {
+                phi_out[gi + nx] = phi_new.y;
+                c_out[gi + nx] = c_new.y;
+                d_out[gi + nx] = d_new.y;
+                if constexpr (sizeof(T) == 4) clo_out[gi + nx] = lo_new.y;
+            }
         }
         fzc_down = fzc;
         fzd_down = fzd;
+    };
+    // thread 0: the out tile of plane k to global memory (after a barrier that
+    // follows the update), one box per state word
+    auto store_tile = [&](int k) {
+        if constexpr (TMA) {
+            if (tid == 0) {
+                tma_store_3d(&tw_phi, sW, x0, y0, k + zpad);
+                tma_store_3d(&tw_c, sW + TX * TY, x0, y0, k + zpad);
+                tma_store_3d(&tw_d, sW + 2 * TX * TY, x0, y0, k + zpad);
+                tma_store_3d(&tw_clo, sW + 3 * TX * TY, x0, y0, k + zpad);
+                bulk_commit();
+            }
+        }
     };
 
     // two phases per plane:
@@ -663,6 +698,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
         if (k > z0) update(k - 1);
         store_plane(ra_p2, rc_p2);
         __syncthreads();
+        if (k > z0) store_tile(k - 1);
         fetch(k + 3, k + 1 < z1, k);
         const bool ghost_up = ghost(k + 1);
         if constexpr (sizeof(T) == 4) {
@@ -705,6 +741,9 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             yface(ra_m1, ra_0, ra_p1, rc_0, rd_0, ex + 2, ex + 1, ec, ed);
             sFy[ex] = nf_y_edge ? vpair(T(0), T(0)) : vpair(ec.y, ed.y);
         }
+        // the next update rewrites the out tile: its stores must have read it
+        if constexpr (TMA)
+            if (tid == 0) bulk_wait_read();
         __syncthreads();
         // rotate the ring offsets to iteration k+1
         const int ta = ra_m1;
@@ -716,10 +755,14 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     }
     fetched();
     update(z1 - 1);
-    // a wait that ran out: give copies still in flight a bounded time to land
-    // before the CTA's shared memory is released
-    if constexpr (TMA)
+    if constexpr (TMA) {
+        __syncthreads();
+        store_tile(z1 - 1);
+        if (tid == 0) bulk_wait_all();
+        // a wait that ran out: give copies still in flight a bounded time to
+        // land before the CTA's shared memory is released
         if (tid == 0 && timed_out) mbar_wait_bounded(bar, stuck);
+    }
 }
 
 // planes per CTA: minimise (waves of resident CTAs) x (planes + prologue) over
@@ -832,7 +875,7 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
     // side) with the staging box.  Rows must be whole multiples of 16 bytes,
     // and a periodic x or y side, whose ghosts come from outside the box, takes
     // per-cell copies.
-    CUtensorMap maps[4];
+    CUtensorMap maps[8];   // inputs phi, c, d, c_lo (staging boxes), outputs (tile boxes)
     std::memset(maps, 0, sizeof(maps));
     int flags = 0;
     const int zpad = (P.bc_lo[2] == PF_BC_HALO || P.bc_hi[2] == PF_BC_HALO) ? 2 : 0;
@@ -842,12 +885,13 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
         const uint64_t n[3] = {(uint64_t)P.n[0], (uint64_t)P.n[1], (uint64_t)P.n[2] + 2 * zpad};
         const uint32_t box[3] = {(uint32_t)L::BXW, (uint32_t)L::BH, 1};
         const size_t plane = (size_t)P.n[0] * P.n[1] * sizeof(T);
-        const void* src[4] = {a.phi_in, a.c_in, a.d_in, a.clo_in};
+        const uint32_t tile[3] = {(uint32_t)TX, (uint32_t)TY, 1};
+        const void* src[8] = {a.phi_in, a.c_in, a.d_in, a.clo_in, a.phi_out, a.c_out, a.d_out, a.clo_out};
         bool ok = true;
-        for (int f = 0; f < (sizeof(T) == 4 ? 4 : 3) && ok; ++f) {
+        for (int f = 0; f < 8 && ok; ++f) {
             const char* base = static_cast<const char*>(src[f]) - zpad * plane;
             ok = reinterpret_cast<uintptr_t>(base) % 16 == 0 &&
-                 encode_tensor_map_3d(&maps[f], sizeof(T) == 8, base, n, box);
+                 encode_tensor_map_3d(&maps[f], sizeof(T) == 8, base, n, f < 4 ? box : tile);
         }
         if (ok) flags |= 1;
     }
@@ -861,7 +905,7 @@ cudaError_t launch_step3d(const StepLaunch& a, const Consts<T>& C, const Clock<T
         static_cast<const T*>(a.phi_in), static_cast<const T*>(a.c_in), static_cast<const T*>(a.d_in),
         static_cast<const T*>(a.clo_in), static_cast<T*>(a.phi_out), static_cast<T*>(a.c_out),
         static_cast<T*>(a.d_out), static_cast<T*>(a.clo_out), K, G, zchunk, zfirst, maps[0], maps[1], maps[2],
-        maps[3], flags, zpad, a.err);
+        maps[3], maps[4], maps[5], maps[6], maps[7], flags, zpad, a.err);
     return cudaGetLastError();
 }
 
