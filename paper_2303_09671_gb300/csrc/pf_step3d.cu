@@ -13,7 +13,10 @@
 //     {phi, Y}, {mu_s, mu_l}, {c_s, c_l} and phi (rings of 4, 4, 3 and 3
 //     planes), the phase-field rate on the halo-1 ring (2 planes) and the
 //     fluxes through the x faces and the upper y face of every cell pair; the
-//     next plane arrives by cp.async in a staging slot;
+//     next plane arrives in a staging slot, in FP32 as tensor-memory-
+//     accelerator boxes (cp.async.bulk.tensor on an mbarrier, issued by one
+//     thread; waits bounded in time), else by per-cell cp.async copies; in
+//     FP32 the updated plane leaves as TMA box stores from a shared tile;
 //   * every thread evaluates the x+1/2, y+1/2 and z+1/2 faces of its own two
 //     cells, so the neighbour records the three faces share are read once;
 //     the faces on the tile's low x and low y edges are evaluated by one more
