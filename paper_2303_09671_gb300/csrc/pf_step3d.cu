@@ -19,8 +19,8 @@
 //     FP32 the updated plane leaves as TMA box stores from a shared tile;
 //   * every thread evaluates the x+1/2, y+1/2 and z+1/2 faces of its own two
 //     cells, so the neighbour records the three faces share are read once;
-//     the faces on the tile's low x and low y edges are evaluated by one more
-//     warp each;
+//     the faces on the tile's low x and low y edges are evaluated by warps 0
+//     and 4;
 //   * a y shift by one cell moves data between the lanes of neighbouring
 //     records; those values are assembled lane by lane, everything else is
 //     two-lane arithmetic;
@@ -112,7 +112,7 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
     constexpr int HW = L::HW, NH = L::NH, NHP = L::NHP, RW = L::RW, FXP = L::FXP;
     constexpr int BXW = L::BXW, BH = L::BH, BOX = L::BOX, RS = L::RS;
     static_assert(HP < 4096, "tile too large for the packed ring descriptors");
-    static_assert(NT >= 32 + TX && TYP <= 32, "edge faces need warps 0 and 1");
+    static_assert(NT >= 128 + TX && TYP <= 32, "edge faces need warps 0 and 4");
     extern __shared__ __align__(128) unsigned char smem[];
     Q* sA = reinterpret_cast<Q*>(smem + L::OFF_A) + L::OQ;
     Q* sB = reinterpret_cast<Q*>(smem + L::OFF_B) + L::OQ;
@@ -737,9 +737,12 @@ step3d_kernel(const T* __restrict__ phi_in, const T* __restrict__ c_in, const T*
             xface(ra_m1, ra_0, ra_p1, rc_0, rd_0, (tid + 1) * HX + 1, (tid + 1) * RX, ec, ed);
             if (nf_x_edge) ec = ed = vpair(T(0), T(0));
             sFx[tid * FXP] = Q{ec, ed};
-        } else if (tid >= 32 && tid < 32 + TX) {
-            // y face on the tile's low y edge (upper lane of the pair row below the tile)
-            const int ex = tid - 32;
+        } else if (tid >= 128 && tid < 128 + TX) {
+            // y face on the tile's low y edge (upper lane of the pair row below the
+            // tile), on warp 4: warps w and w + 4 share a scheduler, and warps 5-7
+            // carry the ring's border rates, so both edge tasks go to the pair
+            // (0, 4) that has no border rate (measured 1.1 % faster than warp 1)
+            const int ex = tid - 128;
             V ec, ed;
             yface(ra_m1, ra_0, ra_p1, rc_0, rd_0, ex + 2, ex + 1, ec, ed);
             sFy[ex] = nf_y_edge ? vpair(T(0), T(0)) : vpair(ec.y, ed.y);
