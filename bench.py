@@ -72,13 +72,13 @@ FP32_LANES, MUFU_LANES = 128, 16    # per SM and clock: FP32 FMA lanes, MUFU res
 # of the kernel's device code the capture ran.  The figure is reported as null
 # as soon as those sources differ from the ones captured.
 TRAFFIC_CAPTURE = {
-    "bytes_per_cell_update": (280.82e6 + 230.53e6) / 256 ** 3,
+    "bytes_per_cell_update": (280.978176e6 + 231.392768e6) / 256 ** 3,
     "captured_grid": 256,
     "sources": ("pf_step3d.cu", "pf_lanes.cuh", "pf_internal.cuh", "pf_tma.cuh"),
-    "sha256": ("ee766988d3aa19decd23f9dd58ec8b5ed0d1976d3cc173a2671d308e4bd373fc",
+    "sha256": ("cc3e6915fa7a0823646513dba91b988aa60f547d9888bd650733450d5b1313cf",
                "1f20de031e00e90a502b3a819635ef32b8ffbda74d768230f9bfa3e8ef2f8e27",
                "47c14bc813e01ef31966d105fe81a4bca92110885cc77bf8470a1be24dce418c",
-               "fea7054fee366693f73adaa753c795cc241657e433ce281527dc8e34f7437f69"),
+               "d0e4d28dc69ba3f9ab24c2a28e424d3fb6e1dc64da959f226126a9eb197caa19"),
 }
 
 
