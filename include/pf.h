@@ -344,7 +344,9 @@ typedef struct {
 } pf_batch_desc;
 
 typedef struct {
-    double* k_v;           /* per instance: last k_v = c_inf / c_max */
+    double* k_v;           /* per instance: last k_v = c_inf / c_max; NaN where the
+                              state stopped being finite (that instance then stops,
+                              with converged = 0) */
     double* dkdt;          /* per instance: last |dk_v/dt| */
     double* t;             /* per instance: simulated time reached */
     int64_t* steps;        /* per instance: steps taken */

@@ -36,7 +36,7 @@ constexpr int BATCH_J = 8;   // cells per thread at most
 struct BatchState {
     long long off;      // offset of the instance's cells in the packed field arrays
     int n;              // cells
-    int converged;
+    int converged;      // 0 running, 1 converged, 2 stopped: the state became non-finite
     long long step, shifts;
     double k_prev, t_prev, k_last, dkdt_last;
 };
@@ -311,17 +311,22 @@ batch_kernel(BatchArgs<T> a) {
         }
         // steady-state check on k_v = c_inf / c_max
         if (a.check_every > 0 && (step % a.check_every) == 0) {
+            // a maximum that keeps a NaN (fmax would drop it): a state that has
+            // stopped being finite must not look steady
+            auto nanmax = [](double x, double y) { return (y > x || y != y) ? y : x; };
             double cm = -1e300;
-            for (int i = tid; i < n; i += NT) cm = fmax(cm, (double)sC[i]);
-            for (int o = 16; o > 0; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+            for (int i = tid; i < n; i += NT) cm = nanmax(cm, (double)sC[i]);
+            for (int o = 16; o > 0; o >>= 1) cm = nanmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
             if ((tid & 31) == 0) red[tid >> 5] = cm;
             __syncthreads();
             if (tid == 0) {
                 double m = red[0];
-                for (int w = 1; w < NT / 32; ++w) m = fmax(m, red[w]);
+                for (int w = 1; w < NT / 32; ++w) m = nanmax(m, red[w]);
                 const double k = a.c_inf / m;
                 k_last = k;
-                if (tn - t_prev >= a.window) {
+                if (!isfinite(m)) {
+                    s_done = 2;   // non-finite state: the instance stops, not converged
+                } else if (tn - t_prev >= a.window) {
                     dkdt_last = fabs(k - k_prev) / (tn - t_prev);
                     s_done = (t_prev > 0.0 && dkdt_last < a.tol && v * tn >= a.min_travel) ? 1 : 0;
                     k_prev = k;
@@ -330,7 +335,7 @@ batch_kernel(BatchArgs<T> a) {
             }
             __syncthreads();
             if (s_done) {
-                converged = 1;
+                converged = s_done;
                 break;
             }
         }
@@ -775,7 +780,7 @@ static int run_batch_T(const pf_batch_desc& D, pf_batch_result* R, cudaStream_t 
         if (R->dkdt) R->dkdt[i] = hs[i].dkdt_last;
         if (R->t) R->t[i] = (double)hs[i].step * B.dt[i];
         if (R->steps) R->steps[i] = hs[i].step;
-        if (R->converged) R->converged[i] = hs[i].converged;
+        if (R->converged) R->converged[i] = hs[i].converged == 1 ? 1 : 0;
     }
     R->cells_per_thread = cpt;
     R->launches = B.launches;

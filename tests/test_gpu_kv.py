@@ -46,3 +46,34 @@ def test_partition_coefficient_falls_towards_k_e_at_low_velocity():
         c = p * res["cs"][i * n:(i + 1) * n] + (1 - p) * res["cl"][i * n:(i + 1) * n]
         behind = c[j[0] - 40:j[0] - 20]
         assert np.abs(behind - cinf).max() <= 1e-3 * cinf, (vs[i], behind)
+
+
+def test_fig3a_trapping_rises_with_A_and_a_blow_up_is_flagged():
+    """Fig. 3(a)'s setting (D_s/D_l = 0.1, b = 1, V = 0.29, i.e. 0.32 m/s for
+    Si-As) in the steep frozen gradient: the batched FP32 fronts for A = 0.9 ..
+    1.5 settle, their c_max falls and k_v rises with A, and each c_max matches
+    the FP64 oracle's steady front to 1e-4.  A = 2 with b = 1 diverges from this
+    start (the printed model's blow-up away from A = 1): that instance stops
+    with converged = 0 and k_v = NaN instead of passing for a steady front."""
+    import oracle
+    n, V = 1024, 0.29
+    cmax, want = [], []
+    for A in (0.9, 1.0, 1.2, 1.5, 2.0):
+        pr, phi, cs, cl = wl.pulled_front_1d(N=n, dx=0.5, V=V, k_e=0.1, D_s=0.1, A=A, b=1.0, G_theta=0.2,
+                                             front_cell=64)
+        dt = min(0.9 * wl.stable_dt(pr), 0.5 * pr["dx"] / V)
+        r = pf.run_batch(pr, [n], [V], *(x.astype(np.float32) for x in (phi, cs, cl)), dt=[dt],
+                         max_steps=200000, steps_per_launch=1000, launches_per_graph=4, check_every=1000,
+                         window=20.0, tol=1e-8, min_travel=200.0)
+        if A == 2.0:
+            assert r["converged"][0] == 0 and np.isnan(r["k_v"][0]), r
+            assert r["steps"][0] < 200000     # stopped early, not run to the cap
+            continue
+        assert r["converged"][0] == 1
+        cmax.append(1.0 / r["k_v"][0])
+        st = oracle.State(dict(pr, dt=dt), phi, cs, cl)
+        st.step(24000)
+        want.append(st.front()[1])
+    assert all(a > b for a, b in zip(cmax, cmax[1:])), cmax
+    for g, w in zip(cmax, want):
+        assert abs(g - w) <= 1e-4 * w, (g, w)
