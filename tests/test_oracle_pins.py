@@ -500,3 +500,24 @@ def test_planted_mistakes_break_the_brute_force_pin(plant):
     got = oracle.State(dict(pr, plant=plant), phi, cs, cl).rates()
     err = max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(got, want))
     assert err > 1e-6, (plant, err)
+
+
+def test_thread_count_does_not_change_the_oracle():
+    """oracle.set_threads (used for the one-thread CPU baseline) changes only
+    how the sweeps are spread: every sweep writes each cell independently and
+    the reductions sum in a fixed order, so one thread and all threads give
+    the same bits."""
+    pr, phi, cs, cl = wl.random_state(3, (20, 11, 9), A=1.5, b=0.3, seed=21)
+    everyone = oracle.num_threads()
+    out = []
+    try:
+        for n in (1, everyone):
+            assert oracle.set_threads(n) == n
+            st = oracle.State(pr, phi, cs, cl)
+            st.step(5)
+            out.append((st.phi.copy(), st.cs.copy(), st.cl.copy(), st.solute(), st.energy()))
+    finally:
+        oracle.set_threads(everyone)
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3] == out[1][3] and out[0][4] == out[1][4]
