@@ -245,10 +245,37 @@ int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void
  * pf_energy needs the same (its gradient pairs reach the ghost planes);
  * pf_solute_total, pf_front, pf_get_fields and pf_set_fields read the slab's
  * own cells only; pf_set_fields_step and pf_step_energies return PF_EINVAL.
+ *
+ * Split step, so that the halo exchange overlaps the step (3D, the fused 3D
+ * kernel): pf_step_begin + pf_step_end advance one step exactly as
+ * pf_step(h, 1) does, bit for bit (the forward-Euler step of Sec. "Numerical
+ * technique").
+ * - pf_step_begin queues the step's interior on a stream of the handle's own,
+ *   ordered after the work already queued on the handle's stream.  The
+ *   interior is the z-chunks of the fused kernel that read only planes
+ *   0 .. n[2]-1 (chunks starting at plane >= 2 and ending at <= n[2]-2).
+ *   It needs no halo.
+ * - The caller then exports its boundary planes and imports its ghost planes
+ *   (pf_get_halo, pf_set_halo; they read and write planes that the interior
+ *   does not touch).
+ * - pf_step_end queues the remaining chunks on the handle's stream, orders
+ *   that stream after the interior, and advances the clock.  It needs every
+ *   halo side imported, as pf_step does; if one is missing it returns
+ *   PF_EINVAL and the split stays open, so the caller can import and call
+ *   pf_step_end again.
+ * Between the two calls pf_step, pf_step_begin, pf_set_fields,
+ * pf_set_fields_step, pf_step_energies and pf_set_clock return PF_EINVAL.
+ * Calls that only read the current state are allowed: the halos, the
+ * fields, the diagnostics.  pf_step_end without an open split returns
+ * PF_EINVAL, and so does pf_step_begin on a 1D or 2D grid or with the
+ * generic kernel (PF_GENERIC).  The handle creates its interior stream on
+ * first use and frees it in pf_destroy, which first waits for it.
  * ------------------------------------------------------------------------ */
 int pf_halo_bytes(pf_handle* h, int64_t* bytes);
 int pf_get_halo(pf_handle* h, int side, void* buf, int where);
 int pf_set_halo(pf_handle* h, int side, const void* buf, int where);
+int pf_step_begin(pf_handle* h);
+int pf_step_end(pf_handle* h);
 
 /* Discrete free energy of Eq. model1.1 for the current state, FP64:
  *   F_h = dV sum_i [H f_dw(phi_i) + p_i f_s,i + (1-p_i) f_l,i]

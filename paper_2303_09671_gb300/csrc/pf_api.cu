@@ -65,6 +65,13 @@ struct pf_handle {
     bool drop_copies = false;    // 3D TMA: copies left out, to test the bounded wait
     bool have_front = false;
     double last_xf = 0.0, last_t = 0.0;
+    // pf_step_begin / pf_step_end: the interior chunks' stream, the event it
+    // waits on (recorded on the handle's stream) and the one it records; split
+    // = a step is open, its interior being chunks [split_lo, split_hi)
+    cudaStream_t sp = nullptr;
+    cudaEvent_t sp_start = nullptr, sp_done = nullptr;
+    bool split = false;
+    int split_lo = 0, split_hi = 0;
     std::string err;
 };
 
@@ -98,6 +105,30 @@ int fail(pf_handle* h, int code, const std::string& msg) {
 
 int cuda_fail(pf_handle* h, cudaError_t e, const char* what) {
     return fail(h, PF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// PF_EINVAL while a split step (pf_step_begin) is open: for the calls that
+// change the state or the clock
+int split_closed(pf_handle* h) {
+    if (h->split) return fail(h, PF_EINVAL, "a split step is open: pf_step_end first");
+    return PF_OK;
+}
+
+// one step from `in` to `out` on stream s, the handle's options; all z-chunks
+pf::StepLaunch step_launch(pf_handle* h, const pf::Fields& in, const pf::Fields& out, cudaStream_t s) {
+    pf::StepLaunch a;
+    a.prob = &h->P;
+    a.phi_in = in.phi; a.c_in = in.c; a.d_in = in.d; a.clo_in = in.clo; a.plo_in = in.plo;
+    a.phi_out = out.phi; a.c_out = out.c; a.d_out = out.d; a.clo_out = out.clo; a.plo_out = out.plo;
+    a.step = h->step;
+    a.shifts = h->shifts;
+    a.zchunk = h->zchunk;
+    a.use_generic = h->generic;
+    a.stream = s;
+    a.err = h->derr;
+    a.no_tma = h->no_tma;
+    a.drop_copies = h->drop_copies;
+    return a;
 }
 
 // order the handle's stream after the state read of a pending
@@ -306,10 +337,14 @@ int pf_create(const pf_grid* grid, const pf_bc* bc, const pf_params* params, voi
 
 void pf_destroy(pf_handle* h) {
     if (!h) return;
+    if (h->sp) cudaStreamSynchronize(h->sp);
     if (h->rb_cv) cudaStreamSynchronize(h->rb_cv);
     if (h->rb) cudaStreamSynchronize(h->rb);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    if (h->sp) cudaStreamDestroy(h->sp);
+    if (h->sp_start) cudaEventDestroy(h->sp_start);
+    if (h->sp_done) cudaEventDestroy(h->sp_done);
     if (h->rb) cudaStreamDestroy(h->rb);
     if (h->rb_cv) cudaStreamDestroy(h->rb_cv);
     if (h->rb_start) cudaEventDestroy(h->rb_start);
@@ -339,6 +374,7 @@ void pf_destroy(pf_handle* h) {
 
 int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl, int where) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = split_closed(h)) return rc;
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE) return fail(h, PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     if (int rc = join_readback(h)) return rc;
@@ -370,6 +406,7 @@ int pf_set_fields(pf_handle* h, const void* phi, const void* cs, const void* cl,
 int pf_set_fields_step(pf_handle* h, const void* phi, const void* cs, const void* cl, int where,
                        int64_t n) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = split_closed(h)) return rc;
     if (!phi || !cs || !cl) return fail(h, PF_EINVAL, "null field pointer");
     if (where != PF_HOST && where != PF_DEVICE && where != PF_HOST_ASYNC)
         return fail(h, PF_EINVAL, "where must be PF_HOST, PF_HOST_ASYNC or PF_DEVICE");
@@ -602,6 +639,8 @@ int pf_sync(pf_handle* h) {
     if (int rc = join_readback(h)) return rc;
     cudaError_t e = cudaSuccess;
     if (h->rb) e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);   // the copies to the host too
+    if (e == cudaSuccess && h->split && h->split_hi > h->split_lo)
+        e = cudaStreamWaitEvent(h->stream, h->sp_done, 0);          // an open split step's interior
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->hres + 4, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
@@ -642,6 +681,7 @@ int pf_get_fields(pf_handle* h, void* phi, void* cs, void* cl, int where) {
 
 int pf_step(pf_handle* h, int64_t n) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = split_closed(h)) return rc;
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
     if (h->halo[0] || h->halo[1]) {
         if (n > 1) return fail(h, PF_EINVAL, "a slab with halo sides steps one step at a time");
@@ -653,20 +693,7 @@ int pf_step(pf_handle* h, int64_t n) {
         if (int rc = join_readback(h)) return rc;
     const pf::HostProblem& P = h->P;
     for (int64_t s = 0; s < n; ++s) {
-        const pf::Fields& in = h->buf[h->cur];
-        const pf::Fields& out = h->buf[h->cur ^ 1];
-        pf::StepLaunch a;
-        a.prob = &P;
-        a.phi_in = in.phi; a.c_in = in.c; a.d_in = in.d; a.clo_in = in.clo; a.plo_in = in.plo;
-        a.phi_out = out.phi; a.c_out = out.c; a.d_out = out.d; a.clo_out = out.clo; a.plo_out = out.plo;
-        a.step = h->step;
-        a.shifts = h->shifts;
-        a.zchunk = h->zchunk;
-        a.use_generic = h->generic;
-        a.stream = h->stream;
-        a.err = h->derr;
-        a.no_tma = h->no_tma;
-        a.drop_copies = h->drop_copies;
+        const pf::StepLaunch a = step_launch(h, h->buf[h->cur], h->buf[h->cur ^ 1], h->stream);
         cudaError_t e = pf::launch_step(a);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
         h->cur ^= 1;
@@ -713,6 +740,7 @@ int pf_energy(pf_handle* h, double* F) {
 
 int pf_step_energies(pf_handle* h, int64_t n, double* F) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = split_closed(h)) return rc;
     if (n < 0) return fail(h, PF_EINVAL, "negative step count");
     if (h->halo[0] || h->halo[1]) return fail(h, PF_EINVAL, "not for a slab with halo sides");
     if (int rc = join_readback(h)) return rc;
@@ -904,6 +932,85 @@ int pf_set_halo(pf_handle* h, int side, const void* buf, int where) {
     return halo_copy(h, side, const_cast<void*>(buf), where, true);
 }
 
+// ---------------------------------------------------------------- split step
+
+// The fused 3D step's z-chunk j covers planes [j zc, min(nz, (j + 1) zc)) and
+// reads planes j zc - 2 .. (j + 1) zc + 1 of its input.  Chunks [*lo, *hi)
+// read only planes 0 .. nz - 1 (start >= 2, end <= nz - 2): the interior,
+// which needs no ghost plane.  *hi <= *lo when there is none.
+static int interior_chunks(pf_handle* h, int* lo, int* hi) {
+    const pf::HostProblem& P = h->P;
+    int zc = 0, nch = 0;
+    cudaError_t e = P.precision == 1 ? pf::step3d_chunks<double>(P, h->zchunk, &zc, &nch)
+                                     : pf::step3d_chunks<float>(P, h->zchunk, &zc, &nch);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step setup");
+    const int nz = (int)P.n[2];
+    *lo = (2 + zc - 1) / zc;
+    *hi = std::min(nch, std::max(0, nz - 2) / zc);
+    return PF_OK;
+}
+
+int pf_step_begin(pf_handle* h) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = split_closed(h)) return rc;
+    if (h->P.dim != 3 || h->generic) return fail(h, PF_EINVAL, "the split step needs a 3D grid and the fused 3D kernel");
+    if (int rc = join_readback(h)) return rc;
+    int lo = 0, hi = 0;
+    if (int rc = interior_chunks(h, &lo, &hi)) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!h->sp) {
+        e = cudaStreamCreateWithFlags(&h->sp, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sp_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sp_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "split-step stream");
+    }
+    if (hi > lo) {
+        // the interior follows everything queued on the handle's stream (the
+        // previous step's last readers of the buffer it writes included)
+        e = cudaEventRecord(h->sp_start, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->sp, h->sp_start, 0);
+        pf::StepLaunch a = step_launch(h, h->buf[h->cur], h->buf[h->cur ^ 1], h->sp);
+        a.zfirst = lo;
+        a.zcount = hi - lo;
+        if (e == cudaSuccess) e = pf::launch_step(a);
+        if (e == cudaSuccess) e = cudaEventRecord(h->sp_done, h->sp);
+        if (e != cudaSuccess) return cuda_fail(h, e, "interior step launch");
+    }
+    h->split = true;
+    h->split_lo = lo;
+    h->split_hi = hi;
+    return PF_OK;
+}
+
+int pf_step_end(pf_handle* h) {
+    if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (!h->split) return fail(h, PF_EINVAL, "no split step is open: pf_step_begin first");
+    if ((h->halo[0] && !h->halo_set[0]) || (h->halo[1] && !h->halo_set[1]))
+        return fail(h, PF_EINVAL, "halo not imported since the last step or pf_set_fields");
+    if (int rc = join_readback(h)) return rc;
+    const int lo = h->split_lo, hi = h->split_hi;
+    h->split = false;
+    pf::StepLaunch a = step_launch(h, h->buf[h->cur], h->buf[h->cur ^ 1], h->stream);
+    cudaError_t e = cudaSuccess;
+    if (hi > lo) {
+        // the chunks below and above the interior, then the join
+        a.zfirst = 0;
+        a.zcount = lo;
+        if (lo > 0) e = pf::launch_step(a);
+        a.zfirst = hi;
+        a.zcount = 1 << 30;   // to the last chunk
+        if (e == cudaSuccess) e = pf::launch_step(a);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->sp_done, 0);
+    } else {
+        e = pf::launch_step(a);   // no interior: every chunk
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "boundary step launch");
+    h->halo_set[0] = h->halo_set[1] = false;
+    h->cur ^= 1;
+    h->step += 1;
+    return PF_OK;
+}
+
 int pf_get_clock(pf_handle* h, int64_t* step, int64_t* shifts) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
     if (!step || !shifts) return fail(h, PF_EINVAL, "null output");
@@ -914,6 +1021,7 @@ int pf_get_clock(pf_handle* h, int64_t* step, int64_t* shifts) {
 
 int pf_set_clock(pf_handle* h, int64_t step, int64_t shifts) {
     if (!h) return fail(nullptr, PF_EINVAL, "null handle");
+    if (int rc = split_closed(h)) return rc;
     if (step < 0 || shifts < 0) return fail(h, PF_EINVAL, "negative clock");
     h->step = step;
     h->shifts = shifts;

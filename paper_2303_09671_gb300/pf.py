@@ -113,6 +113,8 @@ _SIGS = {
     "pf_halo_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "pf_get_halo": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
     "pf_set_halo": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
+    "pf_step_begin": (ctypes.c_int, [_VP]),
+    "pf_step_end": (ctypes.c_int, [_VP]),
     "pf_last_error": (ctypes.c_char_p, [_VP]),
     "pf_destroy": (None, [_VP]),
 }
@@ -338,6 +340,17 @@ class Sim:
         """Import the two ghost planes beyond z side 0 (low) or 1 (high)."""
         ptr, where = self._halo_buf(buf)
         _check(lib().pf_set_halo(self._h, int(side), ptr, where), self._h)
+
+    def step_begin(self):
+        """First half of a split step (3D): queue the z-chunks that read no
+        ghost plane on the handle's interior stream.  Exchange the halos, then
+        call step_end(); the two advance one step as step(1) does."""
+        _check(lib().pf_step_begin(self._h), self._h)
+
+    def step_end(self):
+        """Second half of a split step: the chunks next to the z sides (the
+        halos imported by now), then the join with the interior."""
+        _check(lib().pf_step_end(self._h), self._h)
 
     @property
     def clock(self):

@@ -21,6 +21,11 @@ neighbours.
   before every step, and the grid's diagnostics as reductions over ranks;
 * LocalSlabs: all slabs of a grid in one process on one GPU, the halos
   exchanged by device copies (the decomposition without a second GPU).
+
+Both step by the split step of libpf (pf_step_begin / pf_step_end): the
+z-chunks that read no ghost plane start first, on a stream of the handle's
+own, and the exchange runs beside them; the chunks next to the cuts follow
+once the ghost planes are in.  The result is the same bit for bit.
 """
 from __future__ import annotations
 
@@ -137,11 +142,21 @@ class SlabRun:
             self.sim.set_halo(1, recv_hi)
         self.fresh = True
 
-    def step(self, n: int = 1):
+    def step(self, n: int = 1, overlap: bool = True):
+        """n steps, each after a halo exchange.  overlap: with a handle that
+        has the split step, the exchange runs while the step's interior
+        chunks do (the boundary chunks wait for it)."""
+        split = overlap and self.halo and hasattr(self.sim, "step_begin")
         for _ in range(int(n)):
-            if not self.fresh:
+            if self.fresh:            # halos already in for this state
+                self.sim.step(1)
+            elif split:
+                self.sim.step_begin()
                 self.exchange()
-            self.sim.step(1)
+                self.sim.step_end()
+            else:
+                self.exchange()
+                self.sim.step(1)
             self.fresh = False
 
     def _reduce(self, values, op):
@@ -206,11 +221,19 @@ class LocalSlabs:
                 self.sims[i].get_halo(0, self.buf)
                 self.sims[lo].set_halo(1, self.buf)
 
-    def step(self, n: int = 1):
+    def step(self, n: int = 1, overlap: bool = True):
+        """n steps; overlap: every slab's interior is queued before the
+        exchange, and its boundary chunks after it."""
         for _ in range(int(n)):
+            if overlap:
+                for s in self.sims:
+                    s.step_begin()
             self.exchange()
             for s in self.sims:
-                s.step(1)
+                if overlap:
+                    s.step_end()
+                else:
+                    s.step(1)
 
     def get_fields(self):
         parts = [s.get_fields() for s in self.sims]

@@ -44,12 +44,17 @@ def reference_step(a, periodic):
 
 class FakeSlab:
     """A slab with the halo interface of pf.Sim: own planes plus two ghost
-    planes per side; halo sides must be imported before each step."""
+    planes per side; halo sides must be imported before each step.  Its split
+    step (step_begin / step_end) computes the interior planes from its own
+    planes alone before any ghost is in, and the planes next to the sides in
+    step_end, as the library's split step does."""
 
     def __init__(self, own, halo_lo, halo_hi):
         self.own = own.copy()
         self.halo = (halo_lo, halo_hi)
         self.ghost = [None, None]
+        self.interior = None     # an open split step's interior planes
+        self.splits = 0          # split steps taken
 
     def halo_bytes(self):
         return 2 * self.own[0].size * 8
@@ -61,14 +66,36 @@ class FakeSlab:
     def set_halo(self, side, buf):
         self.ghost[side] = buf.view(torch.float64).numpy().reshape((2,) + self.own.shape[1:]).copy()
 
-    def step(self, n):
-        assert n == 1
+    def _extended(self):
         lo = self.ghost[0] if self.halo[0] else self.own[1::-1]     # mirror: planes 1, 0
         hi = self.ghost[1] if self.halo[1] else self.own[:-3:-1]    # mirror: planes nz-1, nz-2
         assert lo is not None and hi is not None, "halo not imported"
-        ext = np.concatenate([lo, self.own, hi])
+        return np.concatenate([lo, self.own, hi])
+
+    def step(self, n):
+        assert n == 1 and self.interior is None
+        ext = self._extended()
         self.own = sum(w * ext[k:k + self.own.shape[0]] for k, w in enumerate(W))
         self.ghost = [None, None]
+
+    def step_begin(self):
+        assert self.interior is None
+        nz = self.own.shape[0]
+        # planes 2 .. nz-3 read planes 0 .. nz-1 only
+        self.interior = sum(w * self.own[k:k + nz - 4] for k, w in enumerate(W))
+
+    def step_end(self):
+        assert self.interior is not None, "no split step open"
+        ext = self._extended()
+        nz = self.own.shape[0]
+        new = np.empty_like(self.own)
+        new[2:nz - 2] = self.interior
+        for z in (0, 1, nz - 2, nz - 1):
+            new[z] = sum(w * ext[z + k] for k, w in enumerate(W))
+        self.own = new
+        self.ghost = [None, None]
+        self.interior = None
+        self.splits += 1
 
     def energy(self):
         assert all(g is not None for g, h in zip(self.ghost, self.halo) if h), "halo not imported"
@@ -87,7 +114,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, periodic, out):
+def _rank(rank, world, port, periodic, overlap, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -100,10 +127,10 @@ def _rank(rank, world, port, periodic, out):
         fake = FakeSlab(a[z0:z0 + nzl], sp["bc_lo"][2] == "halo", sp["bc_hi"][2] == "halo")
         run = slabs.SlabRun(pr, "fp64", rank, world, dist, sim=fake, device="cpu")
         E = run.energy()
-        run.step(4)
+        run.step(4, overlap=overlap)
         S = run.solute_total()
         fmax, cmax = run.front()
-        out[rank] = (z0, fake.own.copy(), E, S, fmax, cmax)
+        out[rank] = (z0, fake.own.copy(), E, S, fmax, cmax, fake.splits)
     finally:
         dist.barrier()
         dist.destroy_process_group()
@@ -111,11 +138,15 @@ def _rank(rank, world, port, periodic, out):
 
 @pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("periodic", [False, True])
-def test_slab_run_exchange_matches_whole_grid(world, periodic):
+@pytest.mark.parametrize("overlap", [True, False])
+def test_slab_run_exchange_matches_whole_grid(world, periodic, overlap):
+    """Four steps after an energy call (which imports the halos, so the first
+    step is a plain one): with overlap the other three are split steps whose
+    interior is computed before the exchange."""
     port = _free_port()
     with mp.Manager() as m:
         out = m.dict()
-        mp.spawn(_rank, args=(world, port, periodic, out), nprocs=world, join=True)
+        mp.spawn(_rank, args=(world, port, periodic, overlap, out), nprocs=world, join=True)
         res = dict(out)
     nz, ny, nx = 13, 3, 4
     a = np.random.default_rng(5).standard_normal((nz, ny, nx))
@@ -128,6 +159,7 @@ def test_slab_run_exchange_matches_whole_grid(world, periodic):
         assert res[r][2] == pytest.approx(a.sum(), rel=1e-13)
         assert res[r][3] == pytest.approx((ref ** 2).sum(), rel=1e-12)
         assert res[r][4] == ref.max() and res[r][5] == (ref ** 2).max()
+        assert res[r][6] == (3 if overlap else 0)
 
 
 def test_partition_and_neighbours():
