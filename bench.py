@@ -339,8 +339,10 @@ def run_slabs(args, torch, dist, world, rank, local):
     """N > 1: the one 256^3 grid cut into `world` z-slabs, one per rank; before
     every step each rank sends its two boundary planes per cut to its
     neighbours and imports theirs (NCCL point-to-point, 2 x 2 x 256^2 x 16 B =
-    4.2 MB per rank and step), then steps its slab.  Strong scaling: the work
-    is fixed, `value` counts the whole grid's cells."""
+    4.2 MB per rank and step) while the z-chunks of its step that read no
+    ghost plane already run (pf_step_begin), then steps the chunks next to the
+    cuts (pf_step_end).  Strong scaling: the work is fixed, `value` counts the
+    whole grid's cells."""
     from paper_2303_09671_gb300.slabs import SlabRun
     n = args.size
     pr, phi, cs, cl = workload(n)
@@ -394,7 +396,8 @@ def run_slabs(args, torch, dist, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config(n, {"parallelism": f"z-slabs x{world}: NCCL send/recv of 2 ghost planes per cut "
-                                                "and step (pf_get_halo / pf_set_halo)",
+                                                "and step (pf_get_halo / pf_set_halo), overlapped with the "
+                                                "step's interior chunks (pf_step_begin / pf_step_end)",
                                  "scaling_unit": "one grid over all ranks"}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": None,
