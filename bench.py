@@ -593,6 +593,64 @@ def run_kv_to_steady(args):
     return 0
 
 
+def instance_shares(lengths, parts):
+    """Contiguous shares [(first, count)] of the instances for `parts` ranks,
+    cut where the running cell count crosses r / parts of the total, so that
+    every rank steps about the same number of cells; every share holds at
+    least one instance while there are enough."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    n, parts = len(lengths), int(parts)
+    if parts < 1 or parts > n:
+        raise ValueError("need 1 <= parts <= instances")
+    cum = np.cumsum(lengths)
+    cuts = [0]
+    for r in range(1, parts):
+        c = int(np.searchsorted(cum, cum[-1] * r / parts, side="left")) + 1
+        cuts.append(min(max(c, cuts[-1] + 1), n - (parts - r)))
+    cuts.append(n)
+    return [(cuts[r], cuts[r + 1] - cuts[r]) for r in range(parts)]
+
+
+def run_kv_sweep_ranks(args, world, rank, local):
+    """N > 1: the 256 fronts split across ranks by instance_shares, each rank
+    one batched run of its share, no exchange between them.  Strong scaling:
+    the sweep is fixed, `value` counts every rank's instance-steps over the
+    slowest rank's device time."""
+    import datetime
+    import torch
+    import torch.distributed as dist
+    from paper_2303_09671_gb300 import pf
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", init_method="env://", timeout=datetime.timedelta(seconds=300))
+    lengths, vs, prs, dts, phi, cs, cl = kv_sweep_inputs()
+    first, count = instance_shares(lengths, world)[rank]
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    lo, hi = int(off[first]), int(off[first + count])
+    mine = slice(first, first + count)
+    f32 = [np.ascontiguousarray(a[lo:hi], dtype=np.float32) for a in (phi, cs, cl)]
+    K = args.steps
+    spl = max(1, K // 4)
+    kw = dict(dt=dts[mine], steps_per_launch=spl, tol=-1.0)
+    pf.run_batch(prs[0], lengths[mine], vs[mine], *f32, max_steps=spl, launches_per_graph=1, **kw)
+    dist.barrier()
+    res = pf.run_batch(prs[0], lengths[mine], vs[mine], *f32, max_steps=K, launches_per_graph=4, **kw)
+    (batch_s,) = max_over_ranks([res["gpu_ms"] * 1e-3], dist, device="cuda")
+    if rank == 0:
+        cells = int(np.sum(lengths))
+        out = {"metric": "1D pulled-front instance-steps/s (256 instances, 512..8192 cells)",
+               "value": len(lengths) * K / batch_s, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
+               "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
+               "config": {"workload": "kv-sweep: 256 1D pulled fronts, lengths U{512..8192} (seed 4), "
+                                      "V log-spaced 1e-3..10, G=5.25e-3, A=1, b=1, fixed step budget",
+                          "parallelism": f"instances split across {world} ranks by cells, no exchange",
+                          "cells_total": cells},
+               "batch_gpu_s": batch_s, "cell_updates_per_s": cells * K / batch_s}
+        print(json.dumps(out), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_kv_sweep(args):
     """Batched k(V) sweep (one persistent launch per chunk, CUDA graph) against a
     per-instance loop of the single-handle path, same steps, same GPU."""
@@ -600,6 +658,10 @@ def run_kv_sweep(args):
     from paper_2303_09671_gb300 import pf
     if args.to_steady:
         return run_kv_to_steady(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        return run_kv_sweep_ranks(args, world, int(os.environ.get("RANK", "0")),
+                                  int(os.environ.get("LOCAL_RANK", "0")))
     lengths, vs, prs, dts, phi, cs, cl = kv_sweep_inputs()
     K = args.steps
     f32 = [a.astype(np.float32) for a in (phi, cs, cl)]

@@ -1,6 +1,6 @@
 """bench.py's multi-rank bookkeeping (the N > 1 path) on two gloo ranks on
 the CPU: the job time is the slowest rank's, and the weak-scaling rate counts
-every rank's cells."""
+every rank's cells; the split of the kv-sweep's fronts across ranks."""
 import os
 import socket
 import sys
@@ -46,3 +46,29 @@ def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks([3.0, 4.0]) == [3.0, 4.0]
+
+
+def test_instance_shares_cover_and_balance():
+    """The N > 1 kv-sweep split: contiguous shares that cover every instance
+    once, none empty, each within one instance's length of an equal share of
+    the cells."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    lengths = np.random.default_rng(4).integers(512, 8193, size=256)
+    for parts in (1, 2, 3, 4, 8, 256):
+        shares = bench.instance_shares(lengths, parts)
+        assert len(shares) == parts
+        assert shares[0][0] == 0 and sum(c for _, c in shares) == len(lengths)
+        for (f0, c0), (f1, _) in zip(shares, shares[1:]):
+            assert f0 + c0 == f1
+        assert all(c >= 1 for _, c in shares)
+        cells = [int(lengths[f:f + c].sum()) for f, c in shares]
+        if parts < 256:
+            assert max(abs(x - lengths.sum() / parts) for x in cells) <= lengths.max()
+    # a few long instances first: still one instance per rank at least
+    skew = np.array([100000, 100000, 10, 10, 10])
+    shares = bench.instance_shares(skew, 4)
+    assert [c for _, c in shares] and all(c >= 1 for _, c in shares) and sum(c for _, c in shares) == 5
+    with pytest.raises(ValueError):
+        bench.instance_shares(skew, 6)
