@@ -613,15 +613,27 @@ def instance_shares(lengths, parts):
 
 def run_kv_sweep_ranks(args, world, rank, local):
     """N > 1: the 256 fronts split across ranks by instance_shares, each rank
-    one batched run of its share, no exchange between them.  Strong scaling:
-    the sweep is fixed, `value` counts every rank's instance-steps over the
-    slowest rank's device time."""
+    one batched run of its share, no exchange between them (NCCL for the
+    barriers and the max over ranks only)."""
     import datetime
     import torch
     import torch.distributed as dist
     from paper_2303_09671_gb300 import pf
     torch.cuda.set_device(local)
     dist.init_process_group("nccl", init_method="env://", timeout=datetime.timedelta(seconds=300))
+    out = kv_sweep_shard(args, dist, world, rank, pf.run_batch, device="cuda")
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+    return 0
+
+
+def kv_sweep_shard(args, dist, world, rank, run_batch, device):
+    """Rank `rank`'s share of the sweep through run_batch (pf.run_batch's
+    signature), timed by its device milliseconds; rank 0 returns the line
+    (others None).  Strong scaling: the sweep is fixed, `value` counts every
+    rank's instance-steps over the slowest rank's device time."""
     lengths, vs, prs, dts, phi, cs, cl = kv_sweep_inputs()
     first, count = instance_shares(lengths, world)[rank]
     off = np.concatenate([[0], np.cumsum(lengths)])
@@ -631,24 +643,21 @@ def run_kv_sweep_ranks(args, world, rank, local):
     K = args.steps
     spl = max(1, K // 4)
     kw = dict(dt=dts[mine], steps_per_launch=spl, tol=-1.0)
-    pf.run_batch(prs[0], lengths[mine], vs[mine], *f32, max_steps=spl, launches_per_graph=1, **kw)
+    run_batch(prs[0], lengths[mine], vs[mine], *f32, max_steps=spl, launches_per_graph=1, **kw)   # warm-up
     dist.barrier()
-    res = pf.run_batch(prs[0], lengths[mine], vs[mine], *f32, max_steps=K, launches_per_graph=4, **kw)
-    (batch_s,) = max_over_ranks([res["gpu_ms"] * 1e-3], dist, device="cuda")
-    if rank == 0:
-        cells = int(np.sum(lengths))
-        out = {"metric": "1D pulled-front instance-steps/s (256 instances, 512..8192 cells)",
-               "value": len(lengths) * K / batch_s, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
-               "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
-               "config": {"workload": "kv-sweep: 256 1D pulled fronts, lengths U{512..8192} (seed 4), "
-                                      "V log-spaced 1e-3..10, G=5.25e-3, A=1, b=1, fixed step budget",
-                          "parallelism": f"instances split across {world} ranks by cells, no exchange",
-                          "cells_total": cells},
-               "batch_gpu_s": batch_s, "cell_updates_per_s": cells * K / batch_s}
-        print(json.dumps(out), flush=True)
-    dist.barrier()
-    dist.destroy_process_group()
-    return 0
+    res = run_batch(prs[0], lengths[mine], vs[mine], *f32, max_steps=K, launches_per_graph=4, **kw)
+    (batch_s,) = max_over_ranks([res["gpu_ms"] * 1e-3], dist, device=device)
+    if rank != 0:
+        return None
+    cells = int(np.sum(lengths))
+    return {"metric": "1D pulled-front instance-steps/s (256 instances, 512..8192 cells)",
+            "value": len(lengths) * K / batch_s, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
+            "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "kv-sweep: 256 1D pulled fronts, lengths U{512..8192} (seed 4), "
+                                   "V log-spaced 1e-3..10, G=5.25e-3, A=1, b=1, fixed step budget",
+                       "parallelism": f"instances split across {world} ranks by cells, no exchange",
+                       "cells_total": cells},
+            "batch_gpu_s": batch_s, "cell_updates_per_s": cells * K / batch_s}
 
 
 def run_kv_sweep(args):

@@ -72,3 +72,53 @@ def test_instance_shares_cover_and_balance():
     assert [c for _, c in shares] and all(c >= 1 for _, c in shares) and sum(c for _, c in shares) == 5
     with pytest.raises(ValueError):
         bench.instance_shares(skew, 6)
+
+
+def _kv_rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import argparse
+    import numpy as np
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    calls = []
+
+    def fake_run_batch(pr, lengths, vs, phi, cs, cl, *, max_steps, launches_per_graph, dt, steps_per_launch, tol):
+        n = np.asarray(lengths)
+        assert len(phi) == len(cs) == len(cl) == int(n.sum()) and len(vs) == len(n) == len(dt)
+        calls.append((len(n), int(n.sum()), max_steps))
+        return {"gpu_ms": 1e-6 * float(n.sum()) * max_steps * (1.0 + rank)}   # rank 1 slower
+
+    try:
+        line = bench.kv_sweep_shard(argparse.Namespace(steps=400), dist, world, rank, fake_run_batch, "cpu")
+        out[rank] = (calls, line)
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def test_kv_sweep_shards_the_fronts_across_ranks():
+    """bench.py --workload kv-sweep under torchrun, its bookkeeping on two gloo
+    ranks with a stand-in for the batched run: each rank steps its own share
+    (a warm-up, then the timed K steps), the shares cover the 256 fronts, and
+    rank 0 reports all instance-steps over the slowest rank's time."""
+    sys.path.insert(0, ROOT)
+    import bench
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_kv_rank, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    lengths = bench.kv_sweep_inputs()[0]
+    shares = bench.instance_shares(lengths, 2)
+    for rank in (0, 1):
+        calls, _ = res[rank]
+        first, count = shares[rank]
+        cells = int(lengths[first:first + count].sum())
+        assert calls == [(count, cells, 100), (count, cells, 400)]
+    assert res[1][1] is None
+    line = res[0][1]
+    slowest = max(1e-9 * int(lengths[f:f + c].sum()) * 400 * (1 + r) for r, (f, c) in enumerate(shares))
+    assert line["n_gpus"] == 2 and line["scaling"] == "strong"
+    assert line["value"] == pytest.approx(256 * 400 / slowest)
+    assert line["batch_gpu_s"] == pytest.approx(slowest)
